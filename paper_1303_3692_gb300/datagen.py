@@ -1,0 +1,274 @@
+"""Seeded synthetic references and query batches shaped like the paper's workloads.
+
+This module only draws random data; it holds none of the matching method's
+arithmetic, so both the CUDA path and the CPU oracle consume its output.
+Everything is deterministic in the seed (numpy PCG64).
+
+The paper's own data (the first 10^7 nt of a human chromosome 1 contig and
+1024-nt queries mixed from human and mouse contigs, Section V) is not
+available; these recipes stand in for it:
+
+* background: iid bases with P(G)=P(C)=gc/2, P(A)=P(T)=(1-gc)/2;
+* segmental duplications: a random source block of U[1000,10000] bases is
+  copied over a random destination with 1% independent substitutions, until
+  the overwritten bases reach the requested cover (overwrite keeps n exact);
+* tandem repeats: a random unit of U{2..6} bases repeated U{10..200} times,
+  written at a random position, until the cover is reached;
+* repeat families: 4 consensus units of 300 bp and 4 of 6 kb; copies with a
+  per-copy divergence U[0.10,0.20] are written until the cover is reached,
+  about half of the covered bases from each unit size;
+* sampled queries start at U[0, n-m] and receive k substitutions at distinct
+  uniform positions (k uniform over the stated range), each to one of the
+  three other bases; random queries are iid uniform ACGT.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+ASCII = np.frombuffer(b"ACGT", dtype=np.uint8)
+_CHUNK = 1 << 24
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+def background(rng: np.random.Generator, n: int, gc: float = 0.5) -> np.ndarray:
+    """Codes 0..3 (A,C,G,T) drawn iid with the given GC content."""
+    out = np.empty(n, dtype=np.uint8)
+    p = np.cumsum([(1 - gc) / 2, gc / 2, gc / 2])
+    for s in range(0, n, _CHUNK):
+        e = min(n, s + _CHUNK)
+        if gc == 0.5:
+            out[s:e] = rng.integers(0, 4, e - s, dtype=np.uint8)
+        else:
+            u = rng.random(e - s, dtype=np.float32)
+            out[s:e] = np.searchsorted(p.astype(np.float32), u, side="right").astype(np.uint8)
+    return out
+
+
+def _mutate(rng: np.random.Generator, block: np.ndarray, rate: float) -> None:
+    mask = rng.random(block.size) < rate
+    k = int(mask.sum())
+    if k:
+        block[mask] = (block[mask] + rng.integers(1, 4, k, dtype=np.uint8)) & 3
+
+
+def segmental_duplications(rng, codes: np.ndarray, cover: float,
+                           lmin: int = 1000, lmax: int = 10000, sub_rate: float = 0.01) -> None:
+    n = codes.size
+    target = int(cover * n)
+    done = 0
+    if target <= 0 or n <= lmax + 1:
+        return
+    while done < target:
+        L = int(rng.integers(lmin, lmax + 1))
+        src = int(rng.integers(0, n - L + 1))
+        dst = int(rng.integers(0, n - L + 1))
+        block = codes[src:src + L].copy()
+        _mutate(rng, block, sub_rate)
+        codes[dst:dst + L] = block
+        done += L
+
+
+def tandem_repeats(rng, codes: np.ndarray, cover: float,
+                   unit=(2, 6), copies=(10, 200)) -> None:
+    n = codes.size
+    target = int(cover * n)
+    done = 0
+    while done < target:
+        u = int(rng.integers(unit[0], unit[1] + 1))
+        c = int(rng.integers(copies[0], copies[1] + 1))
+        L = u * c
+        if L >= n:
+            break
+        dst = int(rng.integers(0, n - L + 1))
+        codes[dst:dst + L] = np.tile(rng.integers(0, 4, u, dtype=np.uint8), c)
+        done += L
+
+
+def repeat_families(rng, codes: np.ndarray, cover: float, unit_lens=(300, 6000),
+                    n_fam: int = 4, div=(0.10, 0.20)) -> None:
+    n = codes.size
+    cons = {L: [rng.integers(0, 4, L, dtype=np.uint8) for _ in range(n_fam)] for L in unit_lens}
+    target = int(cover * n)
+    per_size = {L: target // len(unit_lens) for L in unit_lens}
+    for L in unit_lens:
+        done = 0
+        if L >= n:
+            continue
+        while done < per_size[L]:
+            block = cons[L][int(rng.integers(0, n_fam))].copy()
+            _mutate(rng, block, float(rng.uniform(div[0], div[1])))
+            dst = int(rng.integers(0, n - L + 1))
+            codes[dst:dst + L] = block
+            done += L
+
+
+def to_ascii(codes: np.ndarray) -> np.ndarray:
+    return ASCII[codes]
+
+
+def reference(n: int, seed: int, gc: float = 0.5, sd_cover: float = 0.0,
+              tandem_cover: float = 0.0, family_cover: float = 0.0) -> np.ndarray:
+    """ASCII reference of n bases built from the recipes above."""
+    rng = _rng(seed)
+    codes = background(rng, n, gc)
+    if family_cover:
+        repeat_families(rng, codes, family_cover)
+    if sd_cover:
+        segmental_duplications(rng, codes, sd_cover)
+    if tandem_cover:
+        tandem_repeats(rng, codes, tandem_cover)
+    return to_ascii(codes)
+
+
+def queries(ref: np.ndarray, nq: int, seed: int, m=100, frac_sampled: float = 0.5,
+            subs=(0, 0)):
+    """Query batch against one ASCII reference.
+
+    m is a fixed length or an inclusive (min, max) range drawn uniformly.
+    Returns (bases uint8 ASCII concatenated, offsets int64 (nq+1), sampled bool).
+    """
+    rng = _rng(seed)
+    n = ref.size
+    if isinstance(m, (tuple, list)):
+        lens = rng.integers(m[0], m[1] + 1, nq).astype(np.int64)
+        mmax = int(m[1])
+    else:
+        lens = np.full(nq, int(m), dtype=np.int64)
+        mmax = int(m)
+    offsets = np.zeros(nq + 1, dtype=np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    sampled = rng.random(nq) < frac_sampled
+    bases = np.empty(int(offsets[-1]), dtype=np.uint8)
+    codes_of = np.full(256, 0, dtype=np.uint8)
+    codes_of[ASCII] = np.arange(4, dtype=np.uint8)
+    step = max(1, (1 << 24) // max(1, mmax))
+    win = np.lib.stride_tricks.sliding_window_view(ref, mmax) if n >= mmax else None
+    for s in range(0, nq, step):
+        e = min(nq, s + step)
+        k = e - s
+        L = lens[s:e]
+        blk = rng.integers(0, 4, (k, mmax), dtype=np.uint8)
+        smp = sampled[s:e].copy()
+        if win is not None:
+            starts = (rng.random(k) * (n - L + 1)).astype(np.int64)
+            starts = np.minimum(starts, n - mmax)
+            # sampled queries shorter than mmax near the end still start <= n-m
+            src = codes_of[win[starts[smp]]]
+            blk[smp] = src
+            nsub = rng.integers(subs[0], subs[1] + 1, k)
+            for j in range(int(subs[1])):
+                sel = smp & (nsub > j)
+                if not sel.any():
+                    continue
+                rows = np.nonzero(sel)[0]
+                # distinct positions: draw position j among the L-j free slots
+                p = (rng.random(rows.size) * (L[rows] - j)).astype(np.int64)
+                if j == 1:
+                    p = np.where(p >= first[rows], p + 1, p)
+                if j == 0:
+                    first = np.full(k, -1, dtype=np.int64)
+                    first[rows] = p
+                blk[rows, p] = (blk[rows, p] + rng.integers(1, 4, rows.size, dtype=np.uint8)) & 3
+        else:
+            smp[:] = False
+        sampled[s:e] = smp
+        mask = np.arange(mmax)[None, :] < L[:, None]
+        bases[offsets[s]:offsets[e]] = ASCII[blk[mask]]
+    return bases, offsets, sampled
+
+
+@dataclass
+class Workload:
+    """One reference plus one query batch (ASCII), with its recipe."""
+    name: str
+    ref: np.ndarray
+    q_bases: np.ndarray
+    q_offsets: np.ndarray
+    sampled: np.ndarray
+    cap: int = 0
+    width: int = 32
+    meta: dict = field(default_factory=dict)
+
+
+SEED0 = 1303369200
+
+# The paper-scale workloads (sizes as stated; see the module docstring for
+# the recipes).  'scale' shrinks n and the query count for quick tests while
+# keeping the recipe.
+
+def plain_small(scale: float = 1.0, seed: int = SEED0 + 1) -> Workload:
+    """1 Mbp iid reference; 100,000 queries of 32 bp, half exact copies, half random."""
+    n = max(64, int(1_000_000 * scale))
+    nq = max(1, int(100_000 * scale))
+    ref = reference(n, seed, gc=0.5)
+    qb, qo, smp = queries(ref, nq, seed + 1000, m=32, frac_sampled=0.5, subs=(0, 0))
+    return Workload("plain-1Mbp-100k-q32", ref, qb, qo, smp, cap=0, width=32,
+                    meta={"n": n, "nq": nq, "m": 32})
+
+
+def repetitive_100m(scale: float = 1.0, seed: int = SEED0 + 2) -> Workload:
+    """100 Mbp reference with 10% segmental duplications and 2% tandem repeats;
+    10,000,000 queries of 100 bp, 80% sampled with 0-2 substitutions, 20% random;
+    locate up to 64 positions."""
+    n = max(20_000, int(100_000_000 * scale))
+    nq = max(1, int(10_000_000 * scale))
+    ref = reference(n, seed, gc=0.5, sd_cover=0.10, tandem_cover=0.02)
+    qb, qo, smp = queries(ref, nq, seed + 1000, m=100, frac_sampled=0.8, subs=(0, 2))
+    return Workload("repetitive-100Mbp-10M-q100", ref, qb, qo, smp, cap=64, width=32,
+                    meta={"n": n, "nq": nq, "m": 100})
+
+
+def human_sized(scale: float = 1.0, seed: int = SEED0 + 4, nq_sampled: int = 100_000_000,
+                nq_random: int = 10_000_000, cap: int = 16) -> Workload:
+    """3.1 Gbp reference at GC 0.41 with 45% repeat families and 3% tandem
+    repeats, int64 suffix array; 150 bp queries, 10^8 sampled with 0-1
+    substitutions plus 10^7 random."""
+    n = max(20_000, int(3_100_000_000 * scale))
+    nq = max(1, int((nq_sampled + nq_random) * scale))
+    ref = reference(n, seed, gc=0.41, family_cover=0.45, tandem_cover=0.03)
+    qb, qo, smp = queries(ref, nq, seed + 1000, m=150,
+                          frac_sampled=nq_sampled / (nq_sampled + nq_random), subs=(0, 1))
+    return Workload("human-3.1Gbp-q150", ref, qb, qo, smp, cap=cap, width=64,
+                    meta={"n": n, "nq": nq, "m": 150})
+
+
+MULTI_REF_SIZES = (5_000_000, 12_000_000, 25_000_000, 50_000_000)
+MULTI_REF_GC = (0.38, 0.45, 0.50, 0.62)
+
+
+def multi_genome(scale: float = 1.0, seed: int = SEED0 + 3):
+    """4 references (5, 12, 25, 50 Mbp; GC 0.38/0.45/0.50/0.62; 5% segmental
+    duplications) and 16,000,000 queries of length U[20,250], each assigned
+    uniformly to one reference, 70% sampled from it and 30% random.
+    Returns (refs, q_bases, q_offsets, q_ref, sampled)."""
+    refs = [reference(max(2_000, int(s * scale)), seed + 10 * i, gc=g, sd_cover=0.05)
+            for i, (s, g) in enumerate(zip(MULTI_REF_SIZES, MULTI_REF_GC))]
+    nq = max(4, int(16_000_000 * scale))
+    rng = _rng(seed + 999)
+    q_ref = rng.integers(0, len(refs), nq).astype(np.uint32)
+    parts = []
+    for r in range(len(refs)):
+        idx = np.nonzero(q_ref == r)[0]
+        qb, qo, smp = queries(refs[r], idx.size, seed + 1000 + r, m=(20, 250),
+                              frac_sampled=0.7, subs=(0, 0))
+        parts.append((idx, qb, qo, smp))
+    lens = np.zeros(nq, dtype=np.int64)
+    sampled = np.zeros(nq, dtype=bool)
+    for idx, qb, qo, smp in parts:
+        lens[idx] = np.diff(qo)
+        sampled[idx] = smp
+    offsets = np.zeros(nq + 1, dtype=np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    bases = np.empty(int(offsets[-1]), dtype=np.uint8)
+    for idx, qb, qo, smp in parts:
+        # scatter each reference's queries into their global slots
+        src_len = np.diff(qo)
+        rows = np.repeat(idx, src_len)
+        within = np.arange(qb.size) - np.repeat(qo[:-1], src_len)
+        bases[offsets[rows] + within] = qb
+    return refs, bases, offsets, q_ref, sampled
