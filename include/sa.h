@@ -1,0 +1,196 @@
+/*
+ * sa.h -- C ABI of libsa.so: batched exact matching of DNA queries against
+ * references by binary search over their suffix arrays, on one NVIDIA GB300
+ * (sm_103a).  Method: Liao et al., "Ultra-fast Multiple Genome Sequence
+ * Matching Using GPU" (arXiv:1303.3692).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Alphabet (Section III): Sigma = {a,c,g,t}; upper and lower case are the
+ *    same base; the order is A < C < G < T.  Any other byte makes the call
+ *    fail with SA_ERR_BASE.
+ *  - Suffix order (Section III, Table I): lexicographic, and a suffix that is
+ *    a proper prefix of another sorts first.
+ *  - Results are half-open: the paper's closed [LB, RB] (Section IV) is
+ *    reported as lo = LB, hi = RB + 1, count = hi - lo.  A query that does not
+ *    occur gets lo = hi = its insertion point and count = 0.  An empty query
+ *    matches every suffix: [0, n).
+ *  - Return value: SA_OK (0) or a negative SA_ERR_* code; sa_strerror() names
+ *    it.  No C++ exception crosses this boundary.  Argument errors are
+ *    detected before any work is queued.
+ *  - Asynchrony: work is queued on the given CUDA stream (NULL = the legacy
+ *    default stream) and the call returns without waiting for it, except
+ *    where a function says otherwise.  Pointers may be device memory or host
+ *    memory (pageable or pinned); host buffers are staged through device
+ *    memory inside the call.  Output written to pinned host memory is valid
+ *    once the stream completes; output to pageable host memory is valid when
+ *    the call returns.
+ *  - Ownership: the caller owns every buffer it passes; the library owns the
+ *    sa_index and its device memory until sa_free().  Scratch device memory
+ *    is taken from a library-private stream-ordered pool and returned on the
+ *    same stream.
+ *  - Threads: calls on distinct streams may run concurrently from different
+ *    host threads.  An sa_index may be searched concurrently; sa_free must not
+ *    race with any use of the index.
+ *  - Devices: an index lives on the device that was current at sa_build /
+ *    sa_load; later calls using it must run with that device current.
+ */
+#ifndef PAPER_1303_3692_GB300_SA_H
+#define PAPER_1303_3692_GB300_SA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define SA_OK 0
+#define SA_ERR_ARG -1      /* invalid argument (null pointer, size, flag, ref id) */
+#define SA_ERR_BASE -2     /* a byte outside {A,C,G,T,a,c,g,t} */
+#define SA_ERR_NOMEM -3    /* device or host allocation failed */
+#define SA_ERR_CUDA -4     /* a CUDA runtime call failed */
+#define SA_ERR_TIMEOUT -5  /* a bounded device-side wait ran out */
+#define SA_ERR_CAPACITY -6 /* an output buffer is too small */
+#define SA_ERR_IO -7       /* file could not be opened, read or written */
+#define SA_ERR_FORMAT -8   /* file is not an index, or its checksum does not match */
+
+/* sa_build flags. */
+#define SA_W32 0x1u /* store the suffix array as uint32 (n < 2^32 - 1) */
+#define SA_W64 0x2u /* store the suffix array as uint64 */
+
+/* Opaque index: 2-bit packed reference, its suffix array and its sampled-key
+ * table, resident in device memory. */
+typedef struct sa_index sa_index;
+
+/* One query's result (Section IV: the SA interval of the query). */
+typedef struct sa_result {
+    uint64_t lo;    /* first suffix-array rank whose suffix has the query as prefix */
+    uint64_t hi;    /* one past the last such rank (= RB + 1) */
+    uint64_t count; /* hi - lo: occurrences of the query in the reference */
+} sa_result;
+
+/* Tuning knobs of the search kernel; zero fields take the defaults.
+ * The results never depend on them. */
+typedef struct sa_search_params {
+    uint32_t threads_per_block; /* 128..1024, multiple of 32 */
+    uint32_t blocks_per_sm;     /* persistent CTAs per SM */
+    uint32_t key_depth;         /* shared-memory key-table depth d (<= the index's) */
+    uint32_t chunk;             /* queries a warp takes from the global counter at once */
+    uint32_t reserved[4];
+} sa_search_params;
+
+/*
+ * sa_build -- index one reference (Section III).
+ *
+ * Packs the bases 2 bits each (A=0, C=1, G=2, T=3, base 0 in the most
+ * significant bits of each 64-bit word), builds the suffix array of the text
+ * on the GPU by prefix doubling (radix sorts of rank pairs; the result is the
+ * unique suffix array of Table I's definition), and samples the key table
+ * that the search keeps in shared memory.
+ *
+ *  text   n bytes of bases, host or device memory.
+ *  n      number of bases, 1 <= n < 2^32 - 1.
+ *  flags  SA_W32 or SA_W64 (exactly one): element width of the suffix array.
+ *  stream CUDA stream (cudaStream_t) or NULL.
+ *  out    receives the new index.
+ *
+ * Synchronous: returns after the index is complete (it synchronizes the
+ * stream) so that SA_ERR_BASE can be reported.  Errors: SA_ERR_ARG, SA_ERR_BASE,
+ * SA_ERR_NOMEM, SA_ERR_CUDA.  On error *out is NULL.
+ */
+int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_index **out);
+
+/*
+ * sa_search_batch -- find the suffix-array interval of every query
+ * (Section IV; Alg. 1 computes the same LB and RB).
+ *
+ *  refs       n_refs index handles (host array).
+ *  n_refs     1..64; all indexes must have the same suffix-array width.
+ *  q_bases    concatenated query bases (host or device).
+ *  q_offsets  n_q + 1 uint64 offsets into q_bases, non-decreasing, q_offsets[0]
+ *             may be non-zero; query i is q_bases[q_offsets[i] .. q_offsets[i+1]).
+ *  q_ref      n_q reference ids (< n_refs), or NULL when n_refs == 1.
+ *  n_q        number of queries (0 is allowed and does nothing).
+ *  out        n_q results (host or device).
+ *  stream     CUDA stream or NULL.
+ *
+ * Errors: SA_ERR_ARG (also for an out-of-range q_ref, detected on the device
+ * and reported for the call when the output is on the host, else left as
+ * lo = hi = count = UINT64_MAX for that query), SA_ERR_BASE (same rule),
+ * SA_ERR_NOMEM, SA_ERR_CUDA.
+ */
+int sa_search_batch(const sa_index *const *refs, uint32_t n_refs, const char *q_bases,
+                    const uint64_t *q_offsets, const uint32_t *q_ref, uint64_t n_q,
+                    sa_result *out, void *stream);
+
+/* sa_search_batch with explicit tuning knobs (params may be NULL). */
+int sa_search_batch_ex(const sa_index *const *refs, uint32_t n_refs, const char *q_bases,
+                       const uint64_t *q_offsets, const uint32_t *q_ref, uint64_t n_q,
+                       sa_result *out, void *stream, const sa_search_params *params);
+
+/*
+ * sa_search_batch_plain -- same contract and results as sa_search_batch, by
+ * the direct GPU rendering of Alg. 1: one thread per query, two independent
+ * full binary searches (LB, then RB) over [-1, n), bases compared one at a
+ * time.  It is the comparison point for the optimized kernel.
+ */
+int sa_search_batch_plain(const sa_index *const *refs, uint32_t n_refs, const char *q_bases,
+                          const uint64_t *q_offsets, const uint32_t *q_ref, uint64_t n_q,
+                          sa_result *out, void *stream);
+
+/*
+ * sa_locate -- text positions of the matches (an extension; the paper
+ * returns only [LB, RB]).
+ *
+ * For query i, writes the first k_i = min(res[i].count, cap) suffix-array
+ * entries res[i].lo, res[i].lo + 1, ... (suffix-array order) to out_pos at
+ * out_offsets[i]; out_offsets (n_q + 1 entries) is the exclusive prefix sum
+ * of k_i and out_offsets[n_q] is the total.
+ *
+ *  refs, n_refs, q_ref   as for sa_search_batch (q_ref selects the index).
+ *  res        n_q results of sa_search_batch (host or device).
+ *  cap        positions kept per query (0 writes offsets of zeros).
+ *  out_offsets n_q + 1 uint64 (host or device).
+ *  out_pos    positions, element width = the indexes' suffix-array width
+ *             (uint32 or uint64); may be NULL to compute only the offsets.
+ *  out_pos_capacity  elements available in out_pos.  Positions whose slot
+ *             is at or beyond it are not written; the caller detects this
+ *             as out_offsets[n_q] > out_pos_capacity.
+ *
+ * Errors: SA_ERR_ARG, SA_ERR_NOMEM, SA_ERR_CUDA.
+ */
+int sa_locate(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_ref,
+              const sa_result *res, uint64_t n_q, uint32_t cap, uint64_t *out_offsets,
+              void *out_pos, uint64_t out_pos_capacity, void *stream);
+
+/* Writes the index (header, packed text, suffix array, key table and a
+ * 64-bit FNV-1a checksum) to path.  Synchronous.  SA_ERR_IO on failure. */
+int sa_save(const sa_index *idx, const char *path, void *stream);
+
+/* Reads an index written by sa_save onto the current device.  Synchronous.
+ * SA_ERR_IO, SA_ERR_FORMAT (bad magic, version or checksum), SA_ERR_NOMEM. */
+int sa_load(const char *path, void *stream, sa_index **out);
+
+/* Size facts of an index; any output pointer may be NULL. */
+int sa_index_info(const sa_index *idx, uint64_t *n, uint32_t *width, uint32_t *key_depth,
+                  uint64_t *device_bytes);
+
+/* Copies the suffix array (n elements of the index's width) to dst (host or
+ * device).  Asynchronous on stream for device/pinned dst. */
+int sa_copy_suffix_array(const sa_index *idx, void *dst, void *stream);
+
+/* Releases the index and its device memory (synchronizes the device first). */
+void sa_free(sa_index *idx);
+
+/* Static English text for a status code. */
+const char *sa_strerror(int status);
+
+/* Library version, e.g. 0x000100 for 0.1.0. */
+uint32_t sa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -1,0 +1,595 @@
+// api.cu -- the extern "C" entry points declared in include/sa.h: argument
+// checks, host/device staging, scratch memory and the index life cycle.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "sa_internal.cuh"
+
+namespace sa {
+
+int status_from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return SA_OK;
+    if (e == cudaErrorMemoryAllocation) return SA_ERR_NOMEM;
+    return SA_ERR_CUDA;
+}
+
+namespace {
+std::mutex g_mu;
+constexpr int kMaxDevices = 64;
+cudaMemPool_t g_pool[kMaxDevices];
+bool g_pool_ok[kMaxDevices];
+int g_sms[kMaxDevices];
+}  // namespace
+
+// Library-private stream-ordered pool: scratch is allocated and released on
+// the caller's stream; the pool keeps freed memory for reuse (trimmed after
+// an index build, whose scratch is large).
+cudaMemPool_t scratch_pool(int dev) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (dev < 0 || dev >= kMaxDevices) return nullptr;
+    if (!g_pool_ok[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        if (cudaMemPoolCreate(&g_pool[dev], &props) != cudaSuccess) return nullptr;
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &thr);
+        g_pool_ok[dev] = true;
+    }
+    return g_pool[dev];
+}
+
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pool = scratch_pool(dev);
+    if (!pool) return cudaErrorMemoryAllocation;
+    return cudaMallocFromPoolAsync(p, bytes ? bytes : 16, pool, s);
+}
+
+void scratch_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+int device_sm_count() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 1;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_sms[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        g_sms[dev] = v > 0 ? v : 1;
+    }
+    return g_sms[dev];
+}
+
+namespace {
+
+bool on_device(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Scratch allocations released on the stream when the call returns.
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void *> ptrs;
+    bool failed = false;
+    template <typename T>
+    T *get(size_t count) {
+        void *p = nullptr;
+        if (failed) return nullptr;
+        if (scratch_alloc(&p, count * sizeof(T) + 16, s) != cudaSuccess) {
+            failed = true;
+            cudaGetLastError();
+            return nullptr;
+        }
+        ptrs.push_back(p);
+        return reinterpret_cast<T *>(p);
+    }
+    ~Scratch() {
+        for (void *p : ptrs) scratch_free(p, s);
+    }
+};
+
+// Device copy of a caller buffer: the pointer itself if it is device memory,
+// else a scratch copy filled on the stream.
+template <typename T>
+const T *device_view(const T *p, size_t count, Scratch &sc, cudaError_t *err) {
+    if (p == nullptr || count == 0 || on_device(p)) return p;
+    T *d = sc.get<T>(count);
+    if (!d) {
+        *err = cudaErrorMemoryAllocation;
+        return nullptr;
+    }
+    cudaError_t e = cudaMemcpyAsync(d, p, count * sizeof(T), cudaMemcpyHostToDevice, sc.s);
+    if (e != cudaSuccess) *err = e;
+    return d;
+}
+
+uint32_t floor_log2(uint64_t x) {
+    uint32_t l = 0;
+    while (x > 1) {
+        x >>= 1;
+        l++;
+    }
+    return l;
+}
+
+constexpr uint32_t kDefaultDepth = 13;
+constexpr uint32_t kSmemBudget = 200 * 1024;
+
+int check_refs(const sa_index *const *refs, uint32_t n_refs, uint32_t *width) {
+    if (!refs || n_refs == 0 || n_refs > SA_MAX_REFS) return SA_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SA_ERR_CUDA;
+    for (uint32_t r = 0; r < n_refs; r++) {
+        if (!refs[r] || refs[r]->device != dev) return SA_ERR_ARG;
+        if (r && refs[r]->width != refs[0]->width) return SA_ERR_ARG;
+    }
+    *width = refs[0]->width;
+    return SA_OK;
+}
+
+// Per-index table depths for one call: each index's own depth, capped by the
+// request, then the deepest tables are trimmed until all fit the budget.
+uint32_t fill_ref_table(const sa_index *const *refs, uint32_t n_refs, uint32_t want_depth, RefTable *t) {
+    uint32_t use[SA_MAX_REFS];
+    for (uint32_t r = 0; r < n_refs; r++) {
+        use[r] = refs[r]->depth < want_depth ? refs[r]->depth : want_depth;
+    }
+    for (;;) {
+        uint32_t total = 0, deepest = 0;
+        for (uint32_t r = 0; r < n_refs; r++) {
+            total += search_table_bytes(use[r]);
+            if (use[r] > use[deepest]) deepest = r;
+        }
+        if (total <= kSmemBudget || use[deepest] == 0) break;
+        use[deepest]--;
+    }
+    uint32_t off = 0;
+    for (uint32_t r = 0; r < n_refs; r++) {
+        const sa_index *x = refs[r];
+        RefDesc &d = t->r[r];
+        d.text = x->text;
+        d.sa = x->sa;
+        d.keys = x->keys;
+        d.keylen = x->keylen;
+        d.n = x->n;
+        d.depth = x->depth;
+        d.use_depth = use[r];
+        d.smem_off = off;
+        d.pad = 0;
+        off += search_table_bytes(use[r]);
+    }
+    return off;
+}
+
+int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_bases, const uint64_t *q_offsets,
+                const uint32_t *q_ref, uint64_t n_q, sa_result *out, void *stream, const sa_search_params *params,
+                bool plain) {
+    uint32_t width = 0;
+    int st = check_refs(refs, n_refs, &width);
+    if (st) return st;
+    if (n_q == 0) return SA_OK;
+    if (!q_offsets || !out || (n_refs > 1 && !q_ref)) return SA_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // First and last offset: read directly, or with one small synchronous copy.
+    uint64_t first = 0, last = 0;
+    const bool off_dev = on_device(q_offsets);
+    if (off_dev) {
+        uint64_t fl[2];
+        cudaError_t e = cudaMemcpyAsync(&fl[0], q_offsets, 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&fl[1], q_offsets + n_q, 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return status_from_cuda(e);
+        first = fl[0];
+        last = fl[1];
+    } else {
+        first = q_offsets[0];
+        last = q_offsets[n_q];
+        for (uint64_t i = 0; i < n_q; i++)
+            if (q_offsets[i + 1] < q_offsets[i]) return SA_ERR_ARG;
+    }
+    if (last < first) return SA_ERR_ARG;
+    const uint64_t total = last - first;
+    if (total > 0 && !q_bases) return SA_ERR_ARG;
+
+    Scratch sc{s};
+    cudaError_t err = cudaSuccess;
+    const char *bases_d = nullptr;
+    if (total > 0) {
+        if (on_device(q_bases)) {
+            bases_d = q_bases + first;
+        } else {
+            char *d = sc.get<char>(total);
+            if (!d) return SA_ERR_NOMEM;
+            err = cudaMemcpyAsync(d, q_bases + first, total, cudaMemcpyHostToDevice, s);
+            bases_d = d;
+        }
+    }
+    const uint64_t *off_d = device_view(q_offsets, n_q + 1, sc, &err);
+    const uint32_t *ref_d = n_refs > 1 || q_ref ? device_view(q_ref, n_q, sc, &err) : nullptr;
+    const bool out_dev = on_device(out);
+    sa_result *out_d = out_dev ? out : sc.get<sa_result>(n_q);
+    const uint64_t nwords = (total >> 5) + n_q + 1;
+    uint64_t *qwords = sc.get<uint64_t>(nwords);
+    int *flags = sc.get<int>(4);  // [0] pack error, [1] status
+    unsigned long long *counter = sc.get<unsigned long long>(1);
+    if (sc.failed) return SA_ERR_NOMEM;
+    if (err != cudaSuccess) return status_from_cuda(err);
+    if ((err = cudaMemsetAsync(flags, 0, 4 * sizeof(int), s)) != cudaSuccess) return status_from_cuda(err);
+    if ((err = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s)) != cudaSuccess)
+        return status_from_cuda(err);
+
+    SearchLaunch L;
+    memset(&L, 0, sizeof L);
+    const uint32_t want_depth = params && params->key_depth ? params->key_depth : kDefaultDepth;
+    L.smem_bytes = fill_ref_table(refs, n_refs, plain ? 0 : want_depth, &L.refs);
+    L.n_refs = n_refs;
+    L.width = width;
+    L.ascii = bases_d;
+    L.qwords = qwords;
+    L.q_off = off_d;
+    L.first = first;
+    L.total = total;
+    L.q_ref = ref_d;
+    L.n_q = n_q;
+    L.out = out_d;
+    L.pack_err = flags;
+    L.counter = counter;
+    L.status = flags + 1;
+    const int sms = device_sm_count();
+    L.threads = params && params->threads_per_block ? params->threads_per_block : 1024;
+    if (L.threads < 32 || L.threads > 1024 || L.threads % 32) return SA_ERR_ARG;
+    const uint32_t bps = params && params->blocks_per_sm ? params->blocks_per_sm : 1;
+    L.blocks = (uint32_t)sms * bps;
+    L.chunk = params && params->chunk ? params->chunk : 64;
+
+    if (total > 0 && (err = launch_pack_queries(bases_d, off_d, first, total, n_q, qwords, flags, s)) != cudaSuccess)
+        return status_from_cuda(err);
+    err = plain ? launch_search_plain(L, s) : launch_search(L, s);
+    if (err != cudaSuccess) return status_from_cuda(err);
+    if (!out_dev) {
+        int hflags[2] = {0, 0};
+        if ((err = cudaMemcpyAsync(out, out_d, n_q * sizeof(sa_result), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return status_from_cuda(err);
+        if ((err = cudaMemcpyAsync(hflags, flags, sizeof hflags, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return status_from_cuda(err);
+        if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return status_from_cuda(err);
+        if (hflags[1]) return hflags[1];
+        if (hflags[0]) return SA_ERR_BASE;
+        for (uint64_t i = 0; i < n_q; i++)
+            if (out[i].lo == ~0ull) return SA_ERR_ARG;
+    }
+    return SA_OK;
+}
+
+void free_index(sa_index *idx) {
+    if (!idx) return;
+    if (idx->text) cudaFree(idx->text);
+    if (idx->sa) cudaFree(idx->sa);
+    if (idx->keys) cudaFree(idx->keys);
+    if (idx->keylen) cudaFree(idx->keylen);
+    delete idx;
+}
+
+uint32_t table_entries(uint32_t depth) { return depth >= 4 ? (1u << depth) : 16u; }
+
+// Allocates the device arrays of an index whose n, width and depth are set.
+int alloc_index(sa_index *idx) {
+    idx->nwords = (idx->n + 31) / 32;
+    const size_t tb = (idx->nwords + SA_PAD_WORDS) * sizeof(uint64_t);
+    const size_t sb = idx->n * (size_t)idx->width;
+    const size_t kb = table_entries(idx->depth) * sizeof(uint4);
+    const size_t lb = table_entries(idx->depth);
+    if (cudaMalloc(&idx->text, tb) != cudaSuccess || cudaMalloc(&idx->sa, sb) != cudaSuccess ||
+        cudaMalloc(&idx->keys, kb) != cudaSuccess || cudaMalloc(&idx->keylen, lb) != cudaSuccess) {
+        cudaGetLastError();
+        return SA_ERR_NOMEM;
+    }
+    idx->device_bytes = tb + sb + kb + lb;
+    return SA_OK;
+}
+
+uint64_t fnv1a(uint64_t h, const void *p, size_t bytes) {
+    const uint8_t *b = reinterpret_cast<const uint8_t *>(p);
+    for (size_t i = 0; i < bytes; i++) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+struct FileHeader {
+    char magic[8];
+    uint32_t version, width;
+    uint64_t n;
+    uint32_t depth, pad;
+    uint64_t nwords;
+    uint64_t checksum;
+};
+
+const char kMagic[8] = {'S', 'A', 'G', 'B', '3', '0', '0', '\0'};
+
+}  // namespace
+}  // namespace sa
+
+using namespace sa;
+
+extern "C" {
+
+int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_index **out) {
+    if (!out) return SA_ERR_ARG;
+    *out = nullptr;
+    if (!text || n == 0 || n >= 0xFFFFFFFFull) return SA_ERR_ARG;
+    const uint32_t wflags = flags & (SA_W32 | SA_W64);
+    if (wflags != SA_W32 && wflags != SA_W64) return SA_ERR_ARG;
+    if (flags & ~(SA_W32 | SA_W64)) return SA_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    sa_index *idx = new (std::nothrow) sa_index();
+    if (!idx) return SA_ERR_NOMEM;
+    if (cudaGetDevice(&idx->device) != cudaSuccess) {
+        delete idx;
+        return SA_ERR_CUDA;
+    }
+    idx->n = n;
+    idx->width = wflags == SA_W32 ? 4 : 8;
+    const uint32_t lg = floor_log2(n);
+    idx->depth = lg < kDefaultDepth ? lg : kDefaultDepth;
+    int st = alloc_index(idx);
+    if (st) {
+        free_index(idx);
+        return st;
+    }
+    {
+        Scratch sc{s};
+        cudaError_t err = cudaSuccess;
+        const char *text_d = device_view(text, n, sc, &err);
+        int *flag = sc.get<int>(1);
+        if (sc.failed) {
+            free_index(idx);
+            return SA_ERR_NOMEM;
+        }
+        int hflag = 0;
+        if (err == cudaSuccess) err = cudaMemsetAsync(flag, 0, sizeof(int), s);
+        if (err == cudaSuccess) err = launch_pack_text(text_d, n, idx->text, idx->nwords + SA_PAD_WORDS, flag, s);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+        if (err != cudaSuccess) {
+            free_index(idx);
+            return status_from_cuda(err);
+        }
+        if (hflag) {
+            free_index(idx);
+            return SA_ERR_BASE;
+        }
+    }
+    st = build_suffix_array(idx, s);
+    if (st == SA_OK) {
+        cudaError_t err = launch_build_keys(idx, s);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+        st = status_from_cuda(err);
+    }
+    cudaMemPoolTrimTo(scratch_pool(idx->device), 0);
+    if (st) {
+        free_index(idx);
+        return st;
+    }
+    *out = idx;
+    return SA_OK;
+}
+
+int sa_search_batch(const sa_index *const *refs, uint32_t n_refs, const char *q_bases, const uint64_t *q_offsets,
+                    const uint32_t *q_ref, uint64_t n_q, sa_result *out, void *stream) {
+    return search_impl(refs, n_refs, q_bases, q_offsets, q_ref, n_q, out, stream, nullptr, false);
+}
+
+int sa_search_batch_ex(const sa_index *const *refs, uint32_t n_refs, const char *q_bases, const uint64_t *q_offsets,
+                       const uint32_t *q_ref, uint64_t n_q, sa_result *out, void *stream,
+                       const sa_search_params *params) {
+    return search_impl(refs, n_refs, q_bases, q_offsets, q_ref, n_q, out, stream, params, false);
+}
+
+int sa_search_batch_plain(const sa_index *const *refs, uint32_t n_refs, const char *q_bases,
+                          const uint64_t *q_offsets, const uint32_t *q_ref, uint64_t n_q, sa_result *out,
+                          void *stream) {
+    return search_impl(refs, n_refs, q_bases, q_offsets, q_ref, n_q, out, stream, nullptr, true);
+}
+
+int sa_locate(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_ref, const sa_result *res,
+              uint64_t n_q, uint32_t cap, uint64_t *out_offsets, void *out_pos, uint64_t out_pos_capacity,
+              void *stream) {
+    uint32_t width = 0;
+    int st = check_refs(refs, n_refs, &width);
+    if (st) return st;
+    if (!out_offsets || (n_q && !res) || (n_refs > 1 && n_q && !q_ref)) return SA_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Scratch sc{s};
+    cudaError_t err = cudaSuccess;
+    const sa_result *res_d = device_view(res, n_q, sc, &err);
+    const uint32_t *ref_d = q_ref ? device_view(q_ref, n_q, sc, &err) : nullptr;
+    const bool off_dev = on_device(out_offsets);
+    uint64_t *off_d = off_dev ? out_offsets : sc.get<uint64_t>(n_q + 1);
+    const bool pos_dev = out_pos == nullptr || on_device(out_pos);
+    void *pos_d = out_pos;
+    if (!pos_dev && out_pos_capacity) pos_d = sc.get<uint8_t>(out_pos_capacity * width);
+    if (!pos_dev && !out_pos_capacity) pos_d = nullptr;
+    const uint64_t tiles = locate_tiles(n_q);
+    uint64_t *partials = sc.get<uint64_t>(tiles + 1);
+    if (sc.failed) return SA_ERR_NOMEM;
+    if (err != cudaSuccess) return status_from_cuda(err);
+    LocateLaunch L;
+    memset(&L, 0, sizeof L);
+    fill_ref_table(refs, n_refs, 0, &L.refs);
+    L.n_refs = n_refs;
+    L.width = width;
+    L.q_ref = ref_d;
+    L.res = res_d;
+    L.n_q = n_q;
+    L.cap = cap;
+    L.out_offsets = off_d;
+    L.out_pos = pos_d;
+    L.capacity = pos_d ? out_pos_capacity : 0;
+    L.partials = partials;
+    if ((err = launch_locate(L, s)) != cudaSuccess) return status_from_cuda(err);
+    if (!off_dev || !pos_dev) {
+        uint64_t total = 0;
+        if ((err = cudaMemcpyAsync(&total, off_d + n_q, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return status_from_cuda(err);
+        if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return status_from_cuda(err);
+        if (!off_dev &&
+            (err = cudaMemcpyAsync(out_offsets, off_d, (n_q + 1) * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return status_from_cuda(err);
+        const uint64_t kept = total < out_pos_capacity ? total : out_pos_capacity;
+        if (!pos_dev && pos_d && kept &&
+            (err = cudaMemcpyAsync(out_pos, pos_d, kept * width, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return status_from_cuda(err);
+        if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return status_from_cuda(err);
+    }
+    return SA_OK;
+}
+
+int sa_save(const sa_index *idx, const char *path, void *stream) {
+    if (!idx || !path) return SA_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t tb = (idx->nwords + SA_PAD_WORDS) * 8, sb = idx->n * (size_t)idx->width;
+    const size_t kb = table_entries(idx->depth) * sizeof(uint4), lb = table_entries(idx->depth);
+    std::vector<uint8_t> buf;
+    try {
+        buf.resize(tb + sb + kb + lb);
+    } catch (...) {
+        return SA_ERR_NOMEM;
+    }
+    cudaError_t e = cudaMemcpyAsync(buf.data(), idx->text, tb, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(buf.data() + tb, idx->sa, sb, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(buf.data() + tb + sb, idx->keys, kb, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(buf.data() + tb + sb + kb, idx->keylen, lb, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    FileHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, kMagic, 8);
+    h.version = 1;
+    h.width = idx->width;
+    h.n = idx->n;
+    h.depth = idx->depth;
+    h.nwords = idx->nwords;
+    h.checksum = fnv1a(14695981039346656037ull, buf.data(), buf.size());
+    FILE *f = fopen(path, "wb");
+    if (!f) return SA_ERR_IO;
+    bool ok = fwrite(&h, sizeof h, 1, f) == 1 && fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+    ok = (fclose(f) == 0) && ok;
+    return ok ? SA_OK : SA_ERR_IO;
+}
+
+int sa_load(const char *path, void *stream, sa_index **out) {
+    if (!path || !out) return SA_ERR_ARG;
+    *out = nullptr;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    FILE *f = fopen(path, "rb");
+    if (!f) return SA_ERR_IO;
+    FileHeader h;
+    if (fread(&h, sizeof h, 1, f) != 1) {
+        fclose(f);
+        return SA_ERR_FORMAT;
+    }
+    if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 1 || (h.width != 4 && h.width != 8) || h.n == 0 ||
+        h.n >= 0xFFFFFFFFull || h.nwords != (h.n + 31) / 32 || h.depth > SA_MAX_KEY_DEPTH) {
+        fclose(f);
+        return SA_ERR_FORMAT;
+    }
+    sa_index *idx = new (std::nothrow) sa_index();
+    if (!idx) {
+        fclose(f);
+        return SA_ERR_NOMEM;
+    }
+    cudaGetDevice(&idx->device);
+    idx->n = h.n;
+    idx->width = h.width;
+    idx->depth = h.depth;
+    const size_t tb = (h.nwords + SA_PAD_WORDS) * 8, sb = h.n * (size_t)h.width;
+    const size_t kb = table_entries(h.depth) * sizeof(uint4), lb = table_entries(h.depth);
+    std::vector<uint8_t> buf;
+    try {
+        buf.resize(tb + sb + kb + lb);
+    } catch (...) {
+        fclose(f);
+        delete idx;
+        return SA_ERR_NOMEM;
+    }
+    const bool rd = fread(buf.data(), 1, buf.size(), f) == buf.size();
+    fclose(f);
+    if (!rd || fnv1a(14695981039346656037ull, buf.data(), buf.size()) != h.checksum) {
+        delete idx;
+        return SA_ERR_FORMAT;
+    }
+    int st = alloc_index(idx);
+    if (st) {
+        free_index(idx);
+        return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(idx->text, buf.data(), tb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(idx->sa, buf.data() + tb, sb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(idx->keys, buf.data() + tb + sb, kb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(idx->keylen, buf.data() + tb + sb + kb, lb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        free_index(idx);
+        return status_from_cuda(e);
+    }
+    *out = idx;
+    return SA_OK;
+}
+
+int sa_index_info(const sa_index *idx, uint64_t *n, uint32_t *width, uint32_t *key_depth, uint64_t *device_bytes) {
+    if (!idx) return SA_ERR_ARG;
+    if (n) *n = idx->n;
+    if (width) *width = idx->width;
+    if (key_depth) *key_depth = idx->depth;
+    if (device_bytes) *device_bytes = idx->device_bytes;
+    return SA_OK;
+}
+
+int sa_copy_suffix_array(const sa_index *idx, void *dst, void *stream) {
+    if (!idx || !dst) return SA_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(dst, idx->sa, idx->n * (size_t)idx->width, cudaMemcpyDefault, s);
+    return status_from_cuda(e);
+}
+
+void sa_free(sa_index *idx) {
+    if (!idx) return;
+    cudaDeviceSynchronize();
+    free_index(idx);
+}
+
+const char *sa_strerror(int status) {
+    switch (status) {
+        case SA_OK: return "success";
+        case SA_ERR_ARG: return "invalid argument";
+        case SA_ERR_BASE: return "byte outside {A,C,G,T,a,c,g,t}";
+        case SA_ERR_NOMEM: return "out of memory";
+        case SA_ERR_CUDA: return "CUDA runtime error";
+        case SA_ERR_TIMEOUT: return "bounded device wait timed out";
+        case SA_ERR_CAPACITY: return "output buffer too small";
+        case SA_ERR_IO: return "file I/O error";
+        case SA_ERR_FORMAT: return "not an index file or checksum mismatch";
+        default: return "unknown status";
+    }
+}
+
+uint32_t sa_version(void) { return 0x000100u; }
+
+}  // extern "C"

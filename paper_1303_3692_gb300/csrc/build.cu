@@ -1,0 +1,247 @@
+// build.cu -- suffix-array construction on the GPU by prefix doubling, and
+// the sampled-key table.  Off the search path; timed apart from it.
+//
+// The paper builds its suffix array on the host (the straightforward sort or
+// DC3, Section III).  Here the text is already packed in device memory, so
+// the array is built there: every suffix is first ranked by its first 29
+// bases (58 bits of packed text plus a 6-bit length that puts a proper prefix
+// first, the order of Table I).  Then, while some group of equal ranks has
+// more than one member, only the members of such groups are re-sorted by the
+// pair (rank[i], rank[i + h]) and h doubles.  Ranks are the suffix-array
+// position of the first member of the group, so they order groups globally
+// and a finished group's rank is its final position.  The radix sorts, scans
+// and compactions come from CUB (a source-only library shipped with the CUDA
+// toolkit); the key computation, rank scatter and key table are kernels here.
+#include <cub/cub.cuh>
+#include <thrust/iterator/counting_iterator.h>
+#include <vector>
+
+#include "sa_internal.cuh"
+
+namespace sa {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+unsigned grid_for(uint64_t n) {
+    uint64_t b = (n + kThreads - 1) / kThreads;
+    const uint64_t cap = (uint64_t)device_sm_count() * 32;
+    if (b > cap) b = cap;
+    return (unsigned)(b ? b : 1);
+}
+
+#define GS_LOOP(i, n) \
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (uint64_t)gridDim.x * blockDim.x)
+
+// Initial key of suffix i: its first 29 bases, then min(29, n - i).  Bits past
+// the text are zero, so equal packed prefixes are ordered by length.
+__global__ void init_keys_kernel(const uint64_t *__restrict__ T, uint64_t n, uint64_t *keys, uint32_t *vals) {
+    GS_LOOP(i, n) {
+        const uint64_t w = text_window(T, i);
+        const uint64_t len = (n - i) < 29 ? (n - i) : 29;
+        keys[i] = (w & ~0x3Full) | len;
+        vals[i] = (uint32_t)i;
+    }
+}
+
+// head value: j if position j starts a group of equal keys, else 0.
+__global__ void head_values_kernel(const uint64_t *__restrict__ keys, uint64_t cnt,
+                                   const uint32_t *__restrict__ pos, uint32_t *hv) {
+    GS_LOOP(t, cnt) {
+        const bool head = t == 0 || keys[t] != keys[t - 1];
+        hv[t] = head ? (pos ? pos[t] : (uint32_t)t) : 0u;
+    }
+}
+
+// After the scan, rank[t] is the SA position of t's group head.  Writes the
+// ranks, the suffix-array entries, and flags members of groups of size > 1.
+__global__ void scatter_ranks_kernel(const uint64_t *__restrict__ keys, uint64_t cnt,
+                                     const uint32_t *__restrict__ pos,   // SA positions (null = identity)
+                                     const uint32_t *__restrict__ sorted_vals, const uint32_t *__restrict__ rank,
+                                     uint32_t *isa, uint32_t *sa, uint8_t *unresolved) {
+    GS_LOOP(t, cnt) {
+        const uint32_t i = sorted_vals[t];
+        const uint32_t j = pos ? pos[t] : (uint32_t)t;
+        sa[j] = i;
+        isa[i] = rank[t];
+        const bool head = t == 0 || keys[t] != keys[t - 1];
+        const bool tail = t + 1 == cnt || keys[t + 1] != keys[t];
+        unresolved[t] = (head && tail) ? 0 : 1;
+    }
+}
+
+// Doubling key of the unresolved member at SA position pos[t].
+__global__ void pair_keys_kernel(const uint32_t *__restrict__ pos, uint64_t cnt, const uint32_t *__restrict__ sa,
+                                 const uint32_t *__restrict__ isa, uint64_t n, uint64_t h, uint64_t *keys,
+                                 uint32_t *vals) {
+    GS_LOOP(t, cnt) {
+        const uint32_t i = sa[pos[t]];
+        const uint64_t r1 = isa[i];
+        const uint64_t r2 = (uint64_t)i + h < n ? (uint64_t)isa[i + h] + 1 : 0;
+        keys[t] = (r1 << 32) | r2;
+        vals[t] = i;
+    }
+}
+
+__global__ void widen_kernel(const uint32_t *__restrict__ src, uint64_t n, uint64_t *dst) {
+    GS_LOOP(i, n) dst[i] = src[i];
+}
+
+struct MaxOp {
+    __device__ __forceinline__ uint32_t operator()(uint32_t a, uint32_t b) const { return a > b ? a : b; }
+};
+
+int bit_length(uint64_t x) {
+    int b = 0;
+    while (x) {
+        b++;
+        x >>= 1;
+    }
+    return b;
+}
+
+struct Pool {
+    cudaStream_t s;
+    std::vector<void *> ptrs;
+    cudaError_t err = cudaSuccess;
+    template <typename T>
+    T *get(size_t count) {
+        void *p = nullptr;
+        if (err != cudaSuccess) return nullptr;
+        err = scratch_alloc(&p, count * sizeof(T) + 16, s);
+        if (err == cudaSuccess) ptrs.push_back(p);
+        return reinterpret_cast<T *>(p);
+    }
+    ~Pool() {
+        for (void *p : ptrs) scratch_free(p, s);
+    }
+};
+
+}  // namespace
+
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) return status_from_cuda(e_); \
+    } while (0)
+
+int build_suffix_array(sa_index *idx, cudaStream_t s) {
+    const uint64_t n = idx->n;
+    Pool pool{s};
+    uint64_t *kA = pool.get<uint64_t>(n), *kB = pool.get<uint64_t>(n);
+    uint32_t *vA = pool.get<uint32_t>(n), *vB = pool.get<uint32_t>(n);
+    uint32_t *isa = pool.get<uint32_t>(n), *sa32 = pool.get<uint32_t>(n);
+    uint32_t *hv = pool.get<uint32_t>(n), *rank = pool.get<uint32_t>(n);
+    uint32_t *posA = pool.get<uint32_t>(n), *posB = pool.get<uint32_t>(n);
+    uint8_t *flag = pool.get<uint8_t>(n);
+    uint64_t *d_count = pool.get<uint64_t>(1);
+    if (pool.err != cudaSuccess) return SA_ERR_NOMEM;
+
+    // Temporary storage sized for the largest call of each CUB routine.
+    size_t t_sort = 0, t_scan = 0, t_sel = 0, t_sel0 = 0;
+    thrust::counting_iterator<uint32_t> iota(0);
+    {
+        cub::DoubleBuffer<uint64_t> kb(kA, kB);
+        cub::DoubleBuffer<uint32_t> vb(vA, vB);
+        CK(cub::DeviceRadixSort::SortPairs(nullptr, t_sort, kb, vb, n, 0, 64, s));
+        CK(cub::DeviceScan::InclusiveScan(nullptr, t_scan, hv, rank, MaxOp(), n, s));
+        CK(cub::DeviceSelect::Flagged(nullptr, t_sel, posA, flag, posB, d_count, n, s));
+        CK(cub::DeviceSelect::Flagged(nullptr, t_sel0, iota, flag, posB, d_count, n, s));
+    }
+    size_t t_bytes = t_sort > t_scan ? t_sort : t_scan;
+    if (t_sel > t_bytes) t_bytes = t_sel;
+    if (t_sel0 > t_bytes) t_bytes = t_sel0;
+    void *temp = pool.get<uint8_t>(t_bytes);
+    if (pool.err != cudaSuccess) return SA_ERR_NOMEM;
+
+    const unsigned g = grid_for(n);
+    // Round 0: rank by the first 29 bases.
+    init_keys_kernel<<<g, kThreads, 0, s>>>(idx->text, n, kA, vA);
+    CK(cudaGetLastError());
+    cub::DoubleBuffer<uint64_t> kb(kA, kB);
+    cub::DoubleBuffer<uint32_t> vb(vA, vB);
+    CK(cub::DeviceRadixSort::SortPairs(temp, t_bytes, kb, vb, n, 0, 64, s));
+    head_values_kernel<<<g, kThreads, 0, s>>>(kb.Current(), n, nullptr, hv);
+    CK(cudaGetLastError());
+    CK(cub::DeviceScan::InclusiveScan(temp, t_bytes, hv, rank, MaxOp(), n, s));
+    scatter_ranks_kernel<<<g, kThreads, 0, s>>>(kb.Current(), n, nullptr, vb.Current(), rank, isa, sa32, flag);
+    CK(cudaGetLastError());
+    // Unresolved SA positions, in increasing order.
+    CK(cub::DeviceSelect::Flagged(temp, t_bytes, iota, flag, posA, d_count, n, s));
+    uint64_t cnt = 0;
+    CK(cudaMemcpyAsync(&cnt, d_count, sizeof cnt, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+
+    const int rank_bits = bit_length(n);
+    uint64_t h = 29;
+    uint32_t *pos = posA, *pos_next = posB;
+    while (cnt > 0) {
+        const unsigned gc = grid_for(cnt);
+        pair_keys_kernel<<<gc, kThreads, 0, s>>>(pos, cnt, sa32, isa, n, h, kA, vA);
+        CK(cudaGetLastError());
+        cub::DoubleBuffer<uint64_t> rk(kA, kB);
+        cub::DoubleBuffer<uint32_t> rv(vA, vB);
+        CK(cub::DeviceRadixSort::SortPairs(temp, t_bytes, rk, rv, cnt, 0, 32 + rank_bits, s));
+        head_values_kernel<<<gc, kThreads, 0, s>>>(rk.Current(), cnt, pos, hv);
+        CK(cudaGetLastError());
+        CK(cub::DeviceScan::InclusiveScan(temp, t_bytes, hv, rank, MaxOp(), cnt, s));
+        scatter_ranks_kernel<<<gc, kThreads, 0, s>>>(rk.Current(), cnt, pos, rv.Current(), rank, isa, sa32, flag);
+        CK(cudaGetLastError());
+        CK(cub::DeviceSelect::Flagged(temp, t_bytes, pos, flag, pos_next, d_count, cnt, s));
+        CK(cudaMemcpyAsync(&cnt, d_count, sizeof cnt, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        uint32_t *tmp = pos;
+        pos = pos_next;
+        pos_next = tmp;
+        h *= 2;
+    }
+    if (idx->width == 4) {
+        CK(cudaMemcpyAsync(idx->sa, sa32, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    } else {
+        widen_kernel<<<g, kThreads, 0, s>>>(sa32, n, reinterpret_cast<uint64_t *>(idx->sa));
+        CK(cudaGetLastError());
+    }
+    CK(cudaStreamSynchronize(s));
+    return SA_OK;
+}
+
+// Key table in level (breadth-first) order: node k >= 1 at level l = floor(log2 k),
+// p = k - 2^l, samples rank floor((2p + 1) n / 2^(l+1)).  Its first 2^d - 1
+// nodes are the table of depth d, so a shallower table is a prefix.  Entry k
+// holds the first 64 bases of that suffix (bits past the text are zero) and
+// keylen[k] = min(64, n - SA[rank]).  Node 0 is unused padding.
+template <typename IdxT>
+__global__ void build_keys_kernel(const uint64_t *__restrict__ T, const IdxT *__restrict__ sa, uint64_t n,
+                                  uint32_t depth, uint32_t entries, uint4 *keys, uint8_t *keylen) {
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < entries; k += gridDim.x * blockDim.x) {
+        uint64_t w0 = 0, w1 = 0;
+        uint32_t len = 0;
+        if (k >= 1 && k < (1u << depth)) {
+            const uint32_t l = 31 - __clz(k);
+            const uint64_t p = k - (1u << l);
+            const uint64_t rank = ((2 * p + 1) * n) >> (l + 1);
+            const uint64_t pos = sa[rank];
+            w0 = text_window(T, pos);
+            w1 = text_window(T, pos + 32);
+            const uint64_t rem = n - pos;
+            len = rem < 64 ? (uint32_t)rem : 64u;
+        }
+        keys[k] = make_uint4((uint32_t)w0, (uint32_t)(w0 >> 32), (uint32_t)w1, (uint32_t)(w1 >> 32));
+        keylen[k] = (uint8_t)len;
+    }
+}
+
+cudaError_t launch_build_keys(sa_index *idx, cudaStream_t s) {
+    const uint32_t entries = idx->depth >= 4 ? (1u << idx->depth) : 16u;
+    const unsigned blocks = (entries + 255) / 256;
+    if (idx->width == 4)
+        build_keys_kernel<uint32_t><<<blocks, 256, 0, s>>>(idx->text, reinterpret_cast<const uint32_t *>(idx->sa),
+                                                           idx->n, idx->depth, entries, idx->keys, idx->keylen);
+    else
+        build_keys_kernel<uint64_t><<<blocks, 256, 0, s>>>(idx->text, reinterpret_cast<const uint64_t *>(idx->sa),
+                                                           idx->n, idx->depth, entries, idx->keys, idx->keylen);
+    return cudaGetLastError();
+}
+
+}  // namespace sa

@@ -1,0 +1,182 @@
+// sa_internal.cuh -- layouts and device helpers shared by the libsa kernels.
+//
+// Packed text layout (Section III alphabet, order A < C < G < T):
+//   base b of a sequence lives in 64-bit word b / 32 at bits
+//   [63 - 2*(b % 32), 62 - 2*(b % 32)], codes A=0 C=1 G=2 T=3.  Big-endian
+//   placement makes unsigned integer comparison of two aligned windows equal
+//   to lexicographic comparison of their bases.  Bits past the end are zero
+//   and every packed text carries SA_PAD_WORDS zero words after its last
+//   word, so a 32-base window starting at any base < n reads in bounds.
+//
+// Packed queries: query q starts at word ((q_offsets[q] - q_offsets[0]) >> 5) + q of the query
+// word buffer.  For consecutive queries this start grows by at least
+// ceil(m_q / 32) words, so no scan is needed to place them.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/sa.h"
+
+#define SA_PAD_WORDS 2
+#define SA_MAX_REFS 64
+#define SA_MAX_KEY_DEPTH 14
+
+namespace sa {
+
+// Device view of one index, passed to the kernels.
+struct RefDesc {
+    const uint64_t *text;   // packed text, nwords + SA_PAD_WORDS words
+    const void *sa;         // n entries of width 4 or 8
+    const uint4 *keys;      // 2^depth key entries: 64 bases as two words (x,y = w0; z,w = w1)
+    const uint8_t *keylen;  // 2^depth clamp lengths min(64, n - SA[rank])
+    uint64_t n;
+    uint32_t depth;         // key-table depth d of this index; K = 2^d - 1 samples
+    uint32_t smem_off;      // byte offset of this table in the search kernel's shared memory
+    uint32_t use_depth;     // depth the search uses (<= depth); 0 = no table
+    uint32_t pad;
+};
+
+// The compare outcome of the three cases of Section IV.
+enum : int { CMP_LESS = -1, CMP_PREFIX = 0, CMP_GREATER = 1 };
+
+__device__ __forceinline__ uint64_t ldg_u64(const uint64_t *p) { return __ldg(p); }
+
+// 32 bases of the packed text starting at base position b (b < n + 32).
+__device__ __forceinline__ uint64_t text_window(const uint64_t *__restrict__ T, uint64_t b) {
+    const uint64_t w = b >> 5;
+    const unsigned sh = (unsigned)(b & 31u) * 2u;
+    const uint64_t a = ldg_u64(T + w);
+    const uint64_t c = ldg_u64(T + w + 1);
+    // (c >> 1) >> (63 - sh) is c >> (64 - sh) for sh > 0 and 0 for sh == 0.
+    return (a << sh) | ((c >> 1) >> (63u - sh));
+}
+
+// Compares query P (packed words Q, length m >= 1) with the m-prefix of the
+// suffix starting at text position p, beginning at base `start` (all bases
+// before it are known equal; start < m).  Returns CMP_LESS if P sorts before
+// the suffix, CMP_PREFIX if P is a prefix of it, CMP_GREATER if P sorts after
+// it (a suffix that ends first sorts before P).  *lcp receives the common
+// prefix length, capped at m.  Windows are 32 bases; the query side is read
+// one aligned word at a time.
+__device__ __forceinline__ int cmp_query_suffix(const uint64_t *__restrict__ T, uint64_t n, uint64_t p,
+                                                const uint64_t *__restrict__ Q, uint32_t m,
+                                                uint32_t start, uint32_t *lcp) {
+    uint32_t off = start & ~31u;
+    const int64_t avail0 = (int64_t)n - (int64_t)p;  // bases left in the suffix
+    for (;;) {
+        const int64_t avail = avail0 - (int64_t)off;
+        const uint32_t qlen = min(32u, m - off);
+        const uint32_t tlen = avail <= 0 ? 0u : (avail >= 32 ? 32u : (uint32_t)avail);
+        const uint64_t q = __ldg(Q + (off >> 5));
+        const uint64_t t = tlen ? text_window(T, p + off) : 0ull;
+        const uint64_t x = q ^ t;
+        const uint32_t d = x ? ((uint32_t)__clzll((long long)x) >> 1) : 32u;
+        const uint32_t lim = min(qlen, tlen);
+        if (d < lim) {
+            *lcp = off + d;
+            return q < t ? CMP_LESS : CMP_GREATER;
+        }
+        if (tlen < qlen) {
+            *lcp = off + tlen;
+            return CMP_GREATER;
+        }
+        if (off + 32u >= m) {
+            *lcp = m;
+            return CMP_PREFIX;
+        }
+        off += 32u;
+    }
+}
+
+// Base code of an ASCII byte; returns 4 for a byte outside {ACGTacgt}.
+__device__ __forceinline__ uint32_t base_code(uint32_t c) {
+    const uint32_t u = c & 0xDFu;  // fold lower case
+    const uint32_t x = (u >> 1) & 3u;  // A:0 C:1 G:3 T:2
+    const uint32_t code = x ^ (x >> 1);  // A:0 C:1 G:2 T:3
+    const bool ok = (u == 'A') | (u == 'C') | (u == 'G') | (u == 'T');
+    return ok ? code : 4u;
+}
+
+template <typename IdxT>
+__device__ __forceinline__ uint64_t sa_at(const void *sa, uint64_t i) {
+    return (uint64_t)__ldg(reinterpret_cast<const IdxT *>(sa) + i);
+}
+
+}  // namespace sa
+
+// ---------------------------------------------------------------------------
+// Host-side internals shared by the translation units.
+// ---------------------------------------------------------------------------
+struct sa_index {
+    uint64_t n;
+    uint32_t width;      // 4 or 8
+    uint32_t depth;      // key-table depth
+    int device;
+    uint64_t nwords;     // packed words without padding
+    uint64_t *text;      // device
+    void *sa;            // device
+    uint4 *keys;         // device, 2^depth entries
+    uint8_t *keylen;     // device, 2^depth entries
+    uint64_t device_bytes;
+};
+
+namespace sa {
+
+int status_from_cuda(cudaError_t e);
+cudaMemPool_t scratch_pool(int device);
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s);
+void scratch_free(void *p, cudaStream_t s);
+int device_sm_count();
+
+// Kernels launched from the API translation unit.
+cudaError_t launch_pack_text(const char *ascii, uint64_t n, uint64_t *words, uint64_t nwords_padded,
+                             int *err_flag, cudaStream_t s);
+cudaError_t launch_pack_queries(const char *ascii, const uint64_t *q_off, uint64_t first, uint64_t total,
+                                uint64_t n_q, uint64_t *qwords, int *err_flag, cudaStream_t s);
+int build_suffix_array(sa_index *idx, cudaStream_t s);
+cudaError_t launch_build_keys(sa_index *idx, cudaStream_t s);
+
+// Descriptors of every index a call uses, passed by value as a kernel
+// parameter (64 x 48 bytes, inside the 4 KB parameter space).
+struct RefTable {
+    RefDesc r[SA_MAX_REFS];
+};
+
+struct SearchLaunch {
+    RefTable refs;
+    uint32_t n_refs;
+    uint32_t width;
+    const char *ascii;        // query bases, indexed by q_off[q] - first
+    const uint64_t *qwords;   // packed queries
+    const uint64_t *q_off;    // n_q + 1 offsets
+    uint64_t first;           // q_off[0]
+    uint64_t total;           // q_off[n_q] - q_off[0]: query ranges past it are invalid
+    const uint32_t *q_ref;    // null when n_refs == 1
+    uint64_t n_q;
+    sa_result *out;
+    const int *pack_err;      // device flag: a query had a non-ACGT byte
+    unsigned long long *counter;
+    int *status;
+    uint32_t smem_bytes;
+    uint32_t threads, blocks, chunk;
+};
+cudaError_t launch_search(const SearchLaunch &L, cudaStream_t s);
+cudaError_t launch_search_plain(const SearchLaunch &L, cudaStream_t s);
+uint32_t search_table_bytes(uint32_t depth);  // shared-memory bytes of a depth-d key table
+
+struct LocateLaunch {
+    RefTable refs;
+    uint32_t n_refs, width;
+    const uint32_t *q_ref;
+    const sa_result *res;
+    uint64_t n_q;
+    uint32_t cap;
+    uint64_t *out_offsets;
+    void *out_pos;
+    uint64_t capacity;
+    uint64_t *partials;       // scratch: one entry per scan tile + 1
+};
+uint64_t locate_tiles(uint64_t n_q);
+cudaError_t launch_locate(const LocateLaunch &L, cudaStream_t s);
+
+}  // namespace sa

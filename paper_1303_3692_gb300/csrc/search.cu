@@ -1,0 +1,465 @@
+// search.cu -- the suffix-array interval of every query (Section IV).
+//
+// Two kernels compute the same [lo, hi):
+//
+// search_kernel (the product path).  Persistent CTAs, one query per lane.
+//   * Each CTA first copies every index's sampled-key table into shared
+//     memory with bulk asynchronous copies (cp.async.bulk, completion on an
+//     mbarrier with a bounded wait).  The table holds the first 64 bases of
+//     the suffixes at ranks floor((2p+1) n / 2^(l+1)) in level order, so
+//     walking it is the first d levels of the binary search, in shared
+//     memory instead of HBM (the paper's tiles, Section IV and V, recast).
+//   * The lower and upper bound move in lockstep while they share an
+//     interval (one probe serves both, the three cases of Section IV) and
+//     split when a pivot's suffix has the query as a prefix.
+//   * A compare starts at min(lcp(P, S_L), lcp(P, S_R)): every suffix between
+//     the bounds shares that prefix with P, so it need not be re-read.  Bases
+//     are compared 32 at a time (an XOR and a count of leading zeros).
+//   * Each lane takes a new query as soon as its own finishes; warps take
+//     chunks of queries from one global counter.  The 32 lanes of a warp
+//     therefore keep 32 independent random probes in flight per load
+//     instruction.
+//
+// search_plain_kernel (comparison point).  Alg. 1 as printed, on a GPU: one
+//   thread per query, two full binary searches over [-1, n), bases compared
+//   one at a time.
+#include "sa_internal.cuh"
+
+namespace sa {
+
+namespace {
+
+struct SmemDesc {
+    const uint64_t *text;
+    const void *sa;
+    uint64_t n;
+    uint32_t off;
+    uint32_t depth;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase with the given parity, giving up after limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+__host__ __device__ __forceinline__ uint32_t table_key_bytes(uint32_t d) { return 16u << d; }
+__host__ __device__ __forceinline__ uint32_t table_len_bytes(uint32_t d) { return d >= 4 ? (1u << d) : 16u; }
+
+// Rank sampled by level-order node k at level l: floor((2p + 1) n / 2^(l+1)).
+__device__ __forceinline__ int64_t node_rank(uint32_t k, uint32_t l, uint64_t n) {
+    const uint64_t p = k - (1u << l);
+    return (int64_t)(((2 * p + 1) * n) >> (l + 1));
+}
+
+// P's first 64 bases (q0, q1) against a 64-base key of length klen.  Sets
+// *undecided when both agree on 64 bases, m > 64 and the key has 64 bases.
+__device__ __forceinline__ int cmp_key(uint64_t q0, uint64_t q1, uint32_t m, uint4 kv, uint32_t klen,
+                                       uint32_t *lcp, bool *undecided) {
+    const uint64_t k0 = ((uint64_t)kv.y << 32) | kv.x;
+    const uint64_t k1 = ((uint64_t)kv.w << 32) | kv.z;
+    uint32_t qlen = min(32u, m), tlen = min(32u, klen);
+    uint64_t x = q0 ^ k0;
+    uint32_t d = x ? ((uint32_t)__clzll((long long)x) >> 1) : 32u;
+    if (d < min(qlen, tlen)) {
+        *lcp = d;
+        return q0 < k0 ? CMP_LESS : CMP_GREATER;
+    }
+    if (tlen < qlen) {
+        *lcp = tlen;
+        return CMP_GREATER;
+    }
+    if (m <= 32) {
+        *lcp = m;
+        return CMP_PREFIX;
+    }
+    qlen = min(32u, m - 32u);
+    tlen = klen > 32u ? min(32u, klen - 32u) : 0u;
+    x = q1 ^ k1;
+    d = x ? ((uint32_t)__clzll((long long)x) >> 1) : 32u;
+    if (d < min(qlen, tlen)) {
+        *lcp = 32u + d;
+        return q1 < k1 ? CMP_LESS : CMP_GREATER;
+    }
+    if (tlen < qlen) {
+        *lcp = 32u + tlen;
+        return CMP_GREATER;
+    }
+    if (m <= 64) {
+        *lcp = m;
+        return CMP_PREFIX;
+    }
+    *undecided = true;
+    *lcp = 64;
+    return CMP_PREFIX;
+}
+
+// Per-lane search state.  Phase 0: both bounds share (L, R).  Phase 1: the
+// lower bound in (L, R] after a split, with the upper bound's interval kept
+// in (HL, HR).  Phase 2: the upper bound.
+struct Lane {
+    int64_t L, R, HL, HR;
+    uint32_t lcpL, lcpR, hlcpL, hlcpR;
+    uint64_t lo;
+    int phase;
+};
+
+// Applies one compare outcome at pivot M.  In phase 0 a prefix match splits
+// the bounds; in phase 1 a prefix moves R (lower bound); in phase 2 it moves L.
+__device__ __forceinline__ void apply(Lane &s, int c, int64_t M, uint32_t l, uint32_t m) {
+    if (c == CMP_PREFIX && s.phase == 0) {
+        s.HL = M;
+        s.hlcpL = m;
+        s.HR = s.R;
+        s.hlcpR = s.lcpR;
+        s.R = M;
+        s.lcpR = m;
+        s.phase = 1;
+    } else if (c == CMP_LESS || (c == CMP_PREFIX && s.phase == 1)) {
+        s.R = M;
+        s.lcpR = l;
+    } else {
+        s.L = M;
+        s.lcpL = l;
+    }
+}
+
+// Moves through finished phases; returns true when the query is done, with
+// its interval in (*lo, *hi).
+__device__ __forceinline__ bool resolve(Lane &s, uint64_t *lo, uint64_t *hi) {
+    for (;;) {
+        if (s.R - s.L > 1) return false;
+        if (s.phase == 0) {
+            *lo = *hi = (uint64_t)s.R;
+            return true;
+        }
+        if (s.phase == 1) {
+            s.lo = (uint64_t)s.R;
+            s.L = s.HL;
+            s.R = s.HR;
+            s.lcpL = s.hlcpL;
+            s.lcpR = s.hlcpR;
+            s.phase = 2;
+            continue;
+        }
+        *lo = s.lo;
+        *hi = (uint64_t)s.R;
+        return true;
+    }
+}
+
+__device__ __forceinline__ void write_result(sa_result *out, uint64_t q, uint64_t lo, uint64_t hi) {
+    sa_result r;
+    r.lo = lo;
+    r.hi = hi;
+    r.count = (lo == ~0ull) ? ~0ull : hi - lo;
+    out[q] = r;
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s for the key-table copy
+
+template <typename IdxT>
+__global__ void __launch_bounds__(1024, 1) search_kernel(const __grid_constant__ SearchLaunch a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ SmemDesc sdesc[SA_MAX_REFS];
+    __shared__ __align__(8) uint64_t mbar;
+    const unsigned tid = threadIdx.x;
+
+    for (unsigned r = tid; r < a.n_refs; r += blockDim.x) {
+        const RefDesc &d = a.refs.r[r];
+        sdesc[r] = SmemDesc{d.text, d.sa, d.n, d.smem_off, d.use_depth};
+    }
+    if (tid == 0) {
+        mbar_init(&mbar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t total = 0;
+        for (uint32_t r = 0; r < a.n_refs; r++) {
+            const uint32_t d = a.refs.r[r].use_depth;
+            if (d) total += table_key_bytes(d) + table_len_bytes(d);
+        }
+        mbar_arrive_expect_tx(&mbar, total);
+        for (uint32_t r = 0; r < a.n_refs; r++) {
+            const RefDesc &d = a.refs.r[r];
+            if (!d.use_depth) continue;
+            bulk_copy_g2s(smem + d.smem_off, d.keys, table_key_bytes(d.use_depth), &mbar);
+            bulk_copy_g2s(smem + d.smem_off + table_key_bytes(d.use_depth), d.keylen, table_len_bytes(d.use_depth),
+                          &mbar);
+        }
+    }
+    if (!mbar_wait_bounded(&mbar, 0, kWaitLimitNs)) {
+        if (tid == 0) atomicExch(a.status, SA_ERR_TIMEOUT);
+        mbar_wait_bounded(&mbar, 0, kWaitLimitNs);  // let copies in flight land before the CTA exits
+        return;
+    }
+
+    const unsigned lane = tid & 31u;
+    const unsigned lanemask_lt = (1u << lane) - 1u;
+    const bool bad_batch = a.pack_err != nullptr && *(volatile const int *)a.pack_err != 0;
+
+    uint64_t pool_next = 0, pool_end = 0;  // warp-uniform chunk of query ids
+    bool exhausted = false;
+    bool active = false, fresh = false;
+    uint64_t q = 0;
+    const uint64_t *Q = nullptr;
+    const uint64_t *T = nullptr;
+    const void *SAp = nullptr;
+    uint64_t n = 0;
+    uint32_t m = 0;
+    Lane s{};
+
+    for (;;) {
+        unsigned need = __ballot_sync(0xFFFFFFFFu, !active);
+        while (need != 0u && !exhausted) {
+            if (pool_next >= pool_end) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(a.counter, (unsigned long long)a.chunk);
+                base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                if (base >= a.n_q) {
+                    exhausted = true;
+                    break;
+                }
+                pool_next = base;
+                pool_end = min((uint64_t)base + a.chunk, a.n_q);
+            }
+            const uint64_t left = pool_end - pool_next;
+            const uint32_t avail = left < 32ull ? (uint32_t)left : 32u;
+            const uint32_t rank = __popc(need & lanemask_lt);
+            if (((need >> lane) & 1u) && rank < avail) {
+                q = pool_next + rank;
+                active = true;
+                fresh = true;
+            }
+            pool_next += min(avail, (uint32_t)__popc(need));
+            need = __ballot_sync(0xFFFFFFFFu, !active);
+        }
+        if (__ballot_sync(0xFFFFFFFFu, active) == 0u) break;
+        if (!active) continue;
+
+        bool done = false;
+        uint64_t lo = 0, hi = 0;
+        if (fresh) {
+            fresh = false;
+            const uint64_t a0 = __ldg(a.q_off + q) - a.first;
+            const uint64_t a1 = __ldg(a.q_off + q + 1) - a.first;
+            const uint32_t r = a.q_ref ? __ldg(a.q_ref + q) : 0u;
+            if (bad_batch || r >= a.n_refs || a1 < a0 || a1 > a.total || a1 - a0 >= (1ull << 31)) {
+                lo = hi = ~0ull;
+                done = true;
+            } else {
+                m = (uint32_t)(a1 - a0);
+                Q = a.qwords + (a0 >> 5) + q;
+                const SmemDesc d = sdesc[r];
+                T = d.text;
+                SAp = d.sa;
+                n = d.n;
+                s.L = -1;
+                s.R = (int64_t)n;
+                s.lcpL = s.lcpR = 0;
+                s.phase = 0;
+                if (m == 0) {
+                    lo = 0;
+                    hi = n;
+                    done = true;
+                } else if (d.depth) {
+                    // Top levels: walk the key table in shared memory.
+                    const uint4 *K = reinterpret_cast<const uint4 *>(smem + d.off);
+                    const uint8_t *KL = smem + d.off + table_key_bytes(d.depth);
+                    const uint64_t q0 = __ldg(Q);
+                    const uint64_t q1 = m > 32 ? __ldg(Q + 1) : 0ull;
+                    uint32_t k = 1, klo = 0, khi = 0;
+                    uint32_t lvl = 0;
+                    // lockstep until a split
+                    for (; lvl < d.depth; lvl++) {
+                        const int64_t M = node_rank(k, lvl, n);
+                        uint32_t l;
+                        bool und = false;
+                        int c = cmp_key(q0, q1, m, K[k], KL[k], &l, &und);
+                        if (und) c = cmp_query_suffix(T, n, sa_at<IdxT>(SAp, (uint64_t)M), Q, m, 64, &l);
+                        apply(s, c, M, l, m);
+                        if (s.phase) {
+                            klo = 2 * k;
+                            khi = 2 * k + 1;
+                            lvl++;
+                            break;
+                        }
+                        k = c == CMP_LESS ? 2 * k : 2 * k + 1;
+                    }
+                    if (s.phase) {
+                        // lower bound in the left subtree, then upper bound in the right one
+                        for (uint32_t l2 = lvl; l2 < d.depth; l2++) {
+                            const int64_t M = node_rank(klo, l2, n);
+                            uint32_t l;
+                            bool und = false;
+                            int c = cmp_key(q0, q1, m, K[klo], KL[klo], &l, &und);
+                            if (und) c = cmp_query_suffix(T, n, sa_at<IdxT>(SAp, (uint64_t)M), Q, m, 64, &l);
+                            apply(s, c, M, l, m);
+                            klo = c <= 0 ? 2 * klo : 2 * klo + 1;
+                        }
+                        Lane h = s;
+                        h.L = s.HL;
+                        h.R = s.HR;
+                        h.lcpL = s.hlcpL;
+                        h.lcpR = s.hlcpR;
+                        h.phase = 2;
+                        for (uint32_t l2 = lvl; l2 < d.depth; l2++) {
+                            const int64_t M = node_rank(khi, l2, n);
+                            uint32_t l;
+                            bool und = false;
+                            int c = cmp_key(q0, q1, m, K[khi], KL[khi], &l, &und);
+                            if (und) c = cmp_query_suffix(T, n, sa_at<IdxT>(SAp, (uint64_t)M), Q, m, 64, &l);
+                            apply(h, c, M, l, m);
+                            khi = c < 0 ? 2 * khi : 2 * khi + 1;
+                        }
+                        s.HL = h.L;
+                        s.HR = h.R;
+                        s.hlcpL = h.lcpL;
+                        s.hlcpR = h.lcpR;
+                    }
+                    done = resolve(s, &lo, &hi);
+                } else {
+                    done = resolve(s, &lo, &hi);
+                }
+            }
+        } else {
+            // One deep probe: the suffix-array entry, then the text it points to.
+            const int64_t M = (s.L + s.R) >> 1;
+            const uint64_t p = sa_at<IdxT>(SAp, (uint64_t)M);
+            uint32_t l;
+            const int c = cmp_query_suffix(T, n, p, Q, m, min(s.lcpL, s.lcpR), &l);
+            apply(s, c, M, l, m);
+            done = resolve(s, &lo, &hi);
+        }
+        if (done) {
+            write_result(a.out, q, lo, hi);
+            active = false;
+        }
+    }
+}
+
+// Alg. 1: compare the query with the m-prefix of S_p one base at a time.
+__device__ __forceinline__ int cmp_plain(const uint64_t *__restrict__ T, uint64_t n, uint64_t p,
+                                         const uint64_t *__restrict__ Q, uint32_t m) {
+    for (uint32_t k = 0; k < m; k++) {
+        if (p + k >= n) return CMP_GREATER;
+        const uint64_t b = p + k;
+        const uint32_t tb = (uint32_t)(__ldg(T + (b >> 5)) >> (62u - 2u * (uint32_t)(b & 31u))) & 3u;
+        const uint32_t qb = (uint32_t)(__ldg(Q + (k >> 5)) >> (62u - 2u * (k & 31u))) & 3u;
+        if (tb != qb) return qb < tb ? CMP_LESS : CMP_GREATER;
+    }
+    return CMP_PREFIX;
+}
+
+template <typename IdxT>
+__global__ void __launch_bounds__(256) search_plain_kernel(const __grid_constant__ SearchLaunch a) {
+    const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= a.n_q) return;
+    const uint64_t a0 = __ldg(a.q_off + q) - a.first;
+    const uint64_t a1 = __ldg(a.q_off + q + 1) - a.first;
+    const uint32_t r = a.q_ref ? __ldg(a.q_ref + q) : 0u;
+    const bool bad = a.pack_err != nullptr && *(volatile const int *)a.pack_err != 0;
+    if (bad || r >= a.n_refs || a1 < a0 || a1 > a.total || a1 - a0 >= (1ull << 31)) {
+        write_result(a.out, q, ~0ull, ~0ull);
+        return;
+    }
+    const uint32_t m = (uint32_t)(a1 - a0);
+    const uint64_t *Q = a.qwords + (a0 >> 5) + q;
+    const RefDesc &d = a.refs.r[r];
+    const uint64_t *T = d.text;
+    const uint64_t n = d.n;
+    // LB: R moves to the pivot while P <= m-prefix of its suffix.
+    int64_t L = -1, R = (int64_t)n;
+    while (R > L + 1) {
+        const int64_t pivot = (L + R) >> 1;
+        if (cmp_plain(T, n, sa_at<IdxT>(d.sa, (uint64_t)pivot), Q, m) <= 0)
+            R = pivot;
+        else
+            L = pivot;
+    }
+    const int64_t LB = R;
+    // RB: R moves to the pivot while P < m-prefix of its suffix.
+    L = -1;
+    R = (int64_t)n;
+    while (R > L + 1) {
+        const int64_t pivot = (L + R) >> 1;
+        if (cmp_plain(T, n, sa_at<IdxT>(d.sa, (uint64_t)pivot), Q, m) < 0)
+            R = pivot;
+        else
+            L = pivot;
+    }
+    const int64_t RB = L;
+    write_result(a.out, q, (uint64_t)LB, (uint64_t)(RB + 1));
+}
+
+}  // namespace
+
+cudaError_t launch_search(const SearchLaunch &L, cudaStream_t s) {
+    if (L.n_q == 0) return cudaSuccess;
+    const size_t smem = L.smem_bytes;
+    if (L.width == 4) {
+        cudaFuncSetAttribute(search_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        search_kernel<uint32_t><<<L.blocks, L.threads, smem, s>>>(L);
+    } else {
+        cudaFuncSetAttribute(search_kernel<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        search_kernel<uint64_t><<<L.blocks, L.threads, smem, s>>>(L);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_search_plain(const SearchLaunch &L, cudaStream_t s) {
+    if (L.n_q == 0) return cudaSuccess;
+    const uint64_t blocks = (L.n_q + 255) / 256;
+    if (L.width == 4)
+        search_plain_kernel<uint32_t><<<(unsigned)blocks, 256, 0, s>>>(L);
+    else
+        search_plain_kernel<uint64_t><<<(unsigned)blocks, 256, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+uint32_t search_table_bytes(uint32_t depth) { return depth ? table_key_bytes(depth) + table_len_bytes(depth) : 0u; }
+
+}  // namespace sa

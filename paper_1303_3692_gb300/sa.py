@@ -1,0 +1,256 @@
+"""Thin ctypes binding of libsa.so (C ABI in include/sa.h).
+
+Argument marshalling only: every step of the search runs in the library's
+CUDA kernels.  Buffers may be torch tensors (CUDA or CPU) or numpy arrays;
+streams are torch.cuda.Stream objects or raw cudaStream_t integers.  The
+binding raises :class:`SAError` with the library's status code on failure and
+refuses to run if the compiled library is missing (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+try:
+    import torch
+except ImportError:  # pragma: no cover - torch is part of the supported stack
+    torch = None
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libsa.so")
+
+SA_OK = 0
+SA_ERR_ARG = -1
+SA_ERR_BASE = -2
+SA_ERR_NOMEM = -3
+SA_ERR_CUDA = -4
+SA_ERR_TIMEOUT = -5
+SA_ERR_CAPACITY = -6
+SA_ERR_IO = -7
+SA_ERR_FORMAT = -8
+SA_W32 = 0x1
+SA_W64 = 0x2
+
+_u64 = ctypes.c_uint64
+_u32 = ctypes.c_uint32
+_vp = ctypes.c_void_p
+
+
+class SAError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {sa_strerror(status)} ({status})" if what else sa_strerror(status))
+
+
+class sa_result(ctypes.Structure):
+    _fields_ = [("lo", _u64), ("hi", _u64), ("count", _u64)]
+
+
+class sa_search_params(ctypes.Structure):
+    _fields_ = [("threads_per_block", _u32), ("blocks_per_sm", _u32), ("key_depth", _u32), ("chunk", _u32),
+                ("reserved", _u32 * 4)]
+
+
+# Every symbol include/sa.h declares, with its ctypes signature.
+SIGNATURES = {
+    "sa_build": (ctypes.c_int, [_vp, _u64, _u32, _vp, ctypes.POINTER(_vp)]),
+    "sa_search_batch": (ctypes.c_int, [ctypes.POINTER(_vp), _u32, _vp, _vp, _vp, _u64, _vp, _vp]),
+    "sa_search_batch_ex": (ctypes.c_int, [ctypes.POINTER(_vp), _u32, _vp, _vp, _vp, _u64, _vp, _vp,
+                                          ctypes.POINTER(sa_search_params)]),
+    "sa_search_batch_plain": (ctypes.c_int, [ctypes.POINTER(_vp), _u32, _vp, _vp, _vp, _u64, _vp, _vp]),
+    "sa_locate": (ctypes.c_int, [ctypes.POINTER(_vp), _u32, _vp, _vp, _u64, _u32, _vp, _vp, _u64, _vp]),
+    "sa_save": (ctypes.c_int, [_vp, ctypes.c_char_p, _vp]),
+    "sa_load": (ctypes.c_int, [ctypes.c_char_p, _vp, ctypes.POINTER(_vp)]),
+    "sa_index_info": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u32), ctypes.POINTER(_u32),
+                                     ctypes.POINTER(_u64)]),
+    "sa_copy_suffix_array": (ctypes.c_int, [_vp, _vp, _vp]),
+    "sa_free": (None, [_vp]),
+    "sa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "sa_version": (_u32, []),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libsa.so is not built ({LIB_PATH}); run "
+                               "paper_1303_3692_gb300.build_lib.build() -- there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def sa_strerror(status: int) -> str:
+    return lib().sa_strerror(int(status)).decode()
+
+
+def _check(status: int, what: str):
+    if status != SA_OK:
+        raise SAError(status, what)
+
+
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if torch is not None and isinstance(x, torch.Tensor):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if isinstance(x, (bytes, bytearray)):
+        raise TypeError("pass bases as a numpy uint8 array or a tensor")
+    raise TypeError(f"unsupported buffer type {type(x)!r}")
+
+
+def _stream(s) -> Optional[int]:
+    if s is None:
+        if torch is not None and torch.cuda.is_available() and torch.cuda.is_initialized():
+            return torch.cuda.current_stream().cuda_stream
+        return None
+    if torch is not None and isinstance(s, torch.cuda.Stream):
+        return s.cuda_stream
+    return int(s)
+
+
+class Index:
+    """A reference indexed on the current device: packed text, suffix array and key table."""
+
+    def __init__(self, handle: int):
+        self._h = _vp(handle)
+        n, w, d, b = _u64(), _u32(), _u32(), _u64()
+        _check(lib().sa_index_info(self._h, ctypes.byref(n), ctypes.byref(w), ctypes.byref(d), ctypes.byref(b)),
+               "sa_index_info")
+        self.n, self.width, self.key_depth, self.device_bytes = n.value, w.value, d.value, b.value
+
+    @property
+    def handle(self):
+        if self._h is None or not self._h.value:
+            raise RuntimeError("index was freed")
+        return self._h
+
+    def free(self):
+        if self._h is not None and self._h.value and _lib is not None:
+            _lib.sa_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def suffix_array(self, device="cuda"):
+        """The suffix array as an int32/int64 tensor (a copy)."""
+        dt = torch.int32 if self.width == 4 else torch.int64
+        out = torch.empty(self.n, dtype=dt, device=device)
+        _check(lib().sa_copy_suffix_array(self.handle, _ptr(out), _stream(None)), "sa_copy_suffix_array")
+        if out.is_cuda:
+            torch.cuda.current_stream().synchronize()
+        return out
+
+    def save(self, path: str):
+        sa_save(self, path)
+
+
+def sa_build(text, width: int = 32, stream=None) -> Index:
+    """Index one reference (ASCII bases, host or device)."""
+    flags = SA_W32 if width == 32 else SA_W64 if width == 64 else None
+    if flags is None:
+        raise ValueError("width must be 32 or 64")
+    n = int(text.numel() if torch is not None and isinstance(text, torch.Tensor) else len(text))
+    h = _vp()
+    _check(lib().sa_build(_ptr(text), n, flags, _stream(stream), ctypes.byref(h)), "sa_build")
+    return Index(h.value)
+
+
+def sa_save(idx: Index, path: str, stream=None):
+    _check(lib().sa_save(idx.handle, os.fsencode(path), _stream(stream)), "sa_save")
+
+
+def sa_load(path: str, stream=None) -> Index:
+    h = _vp()
+    _check(lib().sa_load(os.fsencode(path), _stream(stream), ctypes.byref(h)), "sa_load")
+    return Index(h.value)
+
+
+def sa_free(idx: Index):
+    idx.free()
+
+
+def sa_index_info(idx: Index):
+    return {"n": idx.n, "width": idx.width, "key_depth": idx.key_depth, "device_bytes": idx.device_bytes}
+
+
+def _refs(refs) -> tuple:
+    if isinstance(refs, Index):
+        refs = [refs]
+    arr = (_vp * len(refs))(*[r.handle.value for r in refs])
+    return arr, len(refs)
+
+
+def _out_like(n_q: int, like):
+    dev = like.device if torch is not None and isinstance(like, torch.Tensor) else "cpu"
+    return torch.empty((n_q, 3), dtype=torch.int64, device=dev)
+
+
+def _search(fn, refs, q_bases, q_offsets, q_ref, out, stream, params=None):
+    arr, nr = _refs(refs)
+    n_q = int((q_offsets.numel() if isinstance(q_offsets, torch.Tensor) else len(q_offsets)) - 1)
+    if out is None:
+        out = _out_like(n_q, q_offsets)
+    args = [arr, nr, _ptr(q_bases), _ptr(q_offsets), _ptr(q_ref), n_q, _ptr(out), _stream(stream)]
+    if params is not None:
+        args.append(ctypes.byref(params))
+    _check(fn(*args), fn.__name__)
+    return out
+
+
+def sa_search_batch(refs, q_bases, q_offsets, q_ref=None, out=None, stream=None, params=None):
+    """[lo, hi, count] per query, int64 tensor of shape (n_q, 3); -1 marks an invalid query."""
+    if params is not None:
+        return _search(lib().sa_search_batch_ex, refs, q_bases, q_offsets, q_ref, out, stream, params)
+    return _search(lib().sa_search_batch, refs, q_bases, q_offsets, q_ref, out, stream)
+
+
+def sa_search_batch_plain(refs, q_bases, q_offsets, q_ref=None, out=None, stream=None):
+    """Same results by the one-thread-per-query rendering of Alg. 1."""
+    return _search(lib().sa_search_batch_plain, refs, q_bases, q_offsets, q_ref, out, stream)
+
+
+def sa_locate(refs, res, cap: int, q_ref=None, out_offsets=None, out_pos=None, capacity=None, stream=None):
+    """(offsets (n_q+1), positions) of the first min(count, cap) matches per query.
+
+    With out_pos None, offsets are computed first and a positions tensor of
+    exactly the needed size is allocated on the results' device."""
+    arr, nr = _refs(refs)
+    n_q = int(res.shape[0])
+    dev = res.device if isinstance(res, torch.Tensor) else "cpu"
+    dt = torch.int32 if (refs if isinstance(refs, Index) else refs[0]).width == 4 else torch.int64
+    if out_offsets is None:
+        out_offsets = torch.empty(n_q + 1, dtype=torch.int64, device=dev)
+    s = _stream(stream)
+    if out_pos is None:
+        _check(lib().sa_locate(arr, nr, _ptr(q_ref), _ptr(res), n_q, cap, _ptr(out_offsets), None, 0, s),
+               "sa_locate")
+        total = int(out_offsets[-1].item())
+        out_pos = torch.empty(max(total, 1), dtype=dt, device=dev)
+        capacity = total
+    if capacity is None:
+        capacity = int(out_pos.numel())
+    _check(lib().sa_locate(arr, nr, _ptr(q_ref), _ptr(res), n_q, cap, _ptr(out_offsets), _ptr(out_pos), capacity, s),
+           "sa_locate")
+    return out_offsets, out_pos
