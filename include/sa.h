@@ -73,10 +73,12 @@ typedef struct sa_result {
 /* Tuning knobs of the search kernel; zero fields take the defaults.
  * The results never depend on them. */
 typedef struct sa_search_params {
-    uint32_t threads_per_block; /* 128..1024, multiple of 32 */
+    uint32_t threads_per_block; /* 32..1024, multiple of 32 */
     uint32_t blocks_per_sm;     /* persistent CTAs per SM */
     uint32_t key_depth;         /* shared-memory key-table depth d (<= the index's) */
     uint32_t chunk;             /* queries a warp takes from the global counter at once */
+    void *search_events[2];     /* optional cudaEvent_t pair, recorded on the stream right
+                                   before and after the search kernel (kernel timing) */
     uint32_t reserved[4];
 } sa_search_params;
 
@@ -110,6 +112,10 @@ int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_inde
  *  q_bases    concatenated query bases (host or device).
  *  q_offsets  n_q + 1 uint64 offsets into q_bases, non-decreasing, q_offsets[0]
  *             may be non-zero; query i is q_bases[q_offsets[i] .. q_offsets[i+1]).
+ *             Only the first and last entry are read on the host (with one
+ *             small synchronous copy when the array is in device memory); a
+ *             query whose range is inconsistent with them is reported like a
+ *             non-ACGT byte.
  *  q_ref      n_q reference ids (< n_refs), or NULL when n_refs == 1.
  *  n_q        number of queries (0 is allowed and does nothing).
  *  out        n_q results (host or device).

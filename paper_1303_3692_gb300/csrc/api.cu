@@ -199,8 +199,6 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     } else {
         first = q_offsets[0];
         last = q_offsets[n_q];
-        for (uint64_t i = 0; i < n_q; i++)
-            if (q_offsets[i + 1] < q_offsets[i]) return SA_ERR_ARG;
     }
     if (last < first) return SA_ERR_ARG;
     const uint64_t total = last - first;
@@ -259,8 +257,12 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
 
     if (total > 0 && (err = launch_pack_queries(bases_d, off_d, first, total, n_q, qwords, flags, s)) != cudaSuccess)
         return status_from_cuda(err);
+    cudaEvent_t ev0 = params ? reinterpret_cast<cudaEvent_t>(params->search_events[0]) : nullptr;
+    cudaEvent_t ev1 = params ? reinterpret_cast<cudaEvent_t>(params->search_events[1]) : nullptr;
+    if (ev0 && (err = cudaEventRecord(ev0, s)) != cudaSuccess) return status_from_cuda(err);
     err = plain ? launch_search_plain(L, s) : launch_search(L, s);
     if (err != cudaSuccess) return status_from_cuda(err);
+    if (ev1 && (err = cudaEventRecord(ev1, s)) != cudaSuccess) return status_from_cuda(err);
     if (!out_dev) {
         int hflags[2] = {0, 0};
         if ((err = cudaMemcpyAsync(out, out_d, n_q * sizeof(sa_result), cudaMemcpyDeviceToHost, s)) != cudaSuccess)

@@ -51,7 +51,7 @@ class sa_result(ctypes.Structure):
 
 class sa_search_params(ctypes.Structure):
     _fields_ = [("threads_per_block", _u32), ("blocks_per_sm", _u32), ("key_depth", _u32), ("chunk", _u32),
-                ("reserved", _u32 * 4)]
+                ("search_events", _vp * 2), ("reserved", _u32 * 4)]
 
 
 # Every symbol include/sa.h declares, with its ctypes signature.
@@ -250,7 +250,7 @@ def sa_locate(refs, res, cap: int, q_ref=None, out_offsets=None, out_pos=None, c
         out_pos = torch.empty(max(total, 1), dtype=dt, device=dev)
         capacity = total
     if capacity is None:
-        capacity = int(out_pos.numel())
+        capacity = int(out_pos.numel() if isinstance(out_pos, torch.Tensor) else out_pos.size)
     _check(lib().sa_locate(arr, nr, _ptr(q_ref), _ptr(res), n_q, cap, _ptr(out_offsets), _ptr(out_pos), capacity, s),
            "sa_locate")
     return out_offsets, out_pos

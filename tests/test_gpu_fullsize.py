@@ -1,0 +1,68 @@
+"""Full-size parity on the 100 Mbp repetitive workload (10,000,000 queries of
+100 bp, locate up to 64), in the launch configuration bench.py times: the
+suffix array, every query's [lo, hi, count] and every located position equal
+the oracle's (naive suffix sort + Alg. 1 on the host cores)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_1303_3692_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c2():
+    from paper_1303_3692_gb300 import build_lib, sa
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build_lib.build()
+    w = datagen.repetitive_100m()
+    T = oracle.normalize(w.ref)
+    osa = oracle.sa_naive(T)
+    idx = sa.sa_build(torch.from_numpy(w.ref).cuda())
+    return sa, w, T, osa, idx
+
+
+def test_suffix_array_full_size(c2):
+    sa, w, T, osa, idx = c2
+    got = idx.suffix_array().cpu().numpy().astype(np.int64)
+    assert np.array_equal(got, osa)
+
+
+def test_search_and_locate_full_size(c2):
+    sa, w, T, osa, idx = c2
+    qb = torch.from_numpy(w.q_bases).cuda()
+    qo = torch.from_numpy(w.q_offsets).cuda()
+    res = sa.sa_search_batch(idx, qb, qo)
+    offs, pos = sa.sa_locate(idx, res, w.cap)
+    got = res.cpu().numpy()
+    lo, hi = oracle.search_batch(T, osa, w.q_bases, w.q_offsets, threads=oracle.cpu_threads())
+    assert np.array_equal(got[:, 0], lo)
+    assert np.array_equal(got[:, 1], hi)
+    assert np.array_equal(got[:, 2], hi - lo)
+    k = np.minimum(hi - lo, w.cap)
+    offs = offs.cpu().numpy()
+    assert offs[0] == 0 and np.array_equal(np.diff(offs), k)
+    # expected positions: SA[lo_q + j] for j < k_q, queries in order
+    starts = np.repeat(lo, k)
+    within = np.arange(int(k.sum())) - np.repeat(offs[:-1], k)
+    assert np.array_equal(pos.cpu().numpy().astype(np.int64), osa[starts + within])
+    # every exact copy from the reference occurs; counts agree with brute force on a sample
+    rng = np.random.default_rng(3)
+    for q in rng.choice(np.nonzero(w.sampled)[0], 8, replace=False):
+        P = w.q_bases[w.q_offsets[q]:w.q_offsets[q + 1]]
+        assert oracle.bruteforce(T, P)[0] == hi[q] - lo[q]
+
+
+def test_plain_kernel_full_size_sample(c2):
+    sa, w, T, osa, idx = c2
+    n = 200_000
+    qb = torch.from_numpy(w.q_bases[:w.q_offsets[n]]).cuda()
+    qo = torch.from_numpy(w.q_offsets[:n + 1]).cuda()
+    a = sa.sa_search_batch(idx, qb, qo).cpu()
+    b = sa.sa_search_batch_plain(idx, qb, qo).cpu()
+    assert torch.equal(a, b)

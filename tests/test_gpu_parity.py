@@ -30,7 +30,7 @@ def sa():
 
 
 def _dev(a):
-    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    return torch.from_numpy(np.array(a, copy=True)).to(DEV)
 
 
 def _batch(queries):
@@ -120,7 +120,8 @@ def test_random_references(sa, n, width):
             assert np.array_equal(pos[offs[q]:offs[q + 1]], oracle.locate(osa, int(lo[q]), int(hi[q]), cap))
 
 
-@pytest.mark.parametrize("text", ["A" * 5000, "AC" * 2500, "ACGT" * 1000 + "A", "T" * 33])
+@pytest.mark.parametrize("text", ["A" * 5000, "AC" * 2500, "ACGT" * 1000 + "A", "T" * 33],
+                         ids=["A5000", "AC2500", "ACGT1000A", "T33"])
 def test_degenerate_texts(sa, text):
     T = oracle.normalize(text)
     idx = sa.sa_build(_dev(T))
