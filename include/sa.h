@@ -170,6 +170,41 @@ int sa_locate(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_re
               const sa_result *res, uint64_t n_q, uint32_t cap, uint64_t *out_offsets,
               void *out_pos, uint64_t out_pos_capacity, void *stream);
 
+/* Largest n_q that sa_locate_noalloc accepts (its static scratch holds one
+ * 8-byte partial sum per 4096 queries, plus one: 131,080 bytes). */
+#define SA_LOCATE_NOALLOC_MAX_QUERIES (1ull << 26)
+
+/*
+ * sa_locate_noalloc -- sa_locate for callers that must not allocate device
+ * memory.  The paper has no counterpart; this is a library service.
+ *
+ * Some callers cannot call cudaMalloc: an application whose device memory is
+ * owned up front by another allocator (a framework's caching allocator or a
+ * fixed arena sized at start-up), or a latency-critical loop where an
+ * allocation could block on the device or fail under memory pressure.  This
+ * entry point computes exactly what sa_locate computes but allocates nothing:
+ * the scan's partial sums live in a file-scope __device__ array of
+ * (SA_LOCATE_NOALLOC_MAX_QUERIES / 4096 + 1) uint64 that every device which
+ * loads the library holds until the process exits.
+ *
+ *  Arguments are those of sa_locate, except that res, q_ref (if not NULL),
+ *  out_offsets and out_pos (if not NULL) must all be device memory.
+ *  n_q must be <= SA_LOCATE_NOALLOC_MAX_QUERIES.
+ *
+ * The first call on a device looks up the array's device address for that
+ * device (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  All calls share the one array and it keeps the last call's
+ * contents (no call needs it to start at zero: every partial sum a call reads
+ * is written earlier in the same call), so calls that overlap on the GPU race:
+ * run them on one stream or order them with events.
+ *
+ * Errors: SA_ERR_CAPACITY if n_q exceeds the maximum, SA_ERR_ARG for a host
+ * pointer or any argument sa_locate rejects, SA_ERR_CUDA.
+ */
+int sa_locate_noalloc(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_ref,
+                      const sa_result *res, uint64_t n_q, uint32_t cap, uint64_t *out_offsets,
+                      void *out_pos, uint64_t out_pos_capacity, void *stream);
+
 /* Writes the index (header, packed text, suffix array, key table and a
  * 64-bit FNV-1a checksum) to path.  Synchronous.  SA_ERR_IO on failure. */
 int sa_save(const sa_index *idx, const char *path, void *stream);

@@ -463,6 +463,39 @@ int sa_locate(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_re
     return SA_OK;
 }
 
+// sa_locate without allocation: device buffers only, scan scratch in the
+// static array of locate.cu (see include/sa.h for who needs this and why).
+int sa_locate_noalloc(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_ref, const sa_result *res,
+                      uint64_t n_q, uint32_t cap, uint64_t *out_offsets, void *out_pos, uint64_t out_pos_capacity,
+                      void *stream) {
+    if (n_q > SA_LOCATE_NOALLOC_MAX_QUERIES) return SA_ERR_CAPACITY;
+    uint32_t width = 0;
+    int st = check_refs(refs, n_refs, &width);
+    if (st) return st;
+    if (!out_offsets || (n_q && !res) || (n_refs > 1 && n_q && !q_ref)) return SA_ERR_ARG;
+    if (!on_device(out_offsets) || (n_q && !on_device(res)) || (q_ref && !on_device(q_ref)) ||
+        (out_pos && !on_device(out_pos)))
+        return SA_ERR_ARG;
+    uint64_t *partials = nullptr, entries = 0;
+    cudaError_t err = locate_static_partials(&partials, &entries);
+    if (err != cudaSuccess) return status_from_cuda(err);
+    if (locate_tiles(n_q) + 1 > entries) return SA_ERR_CAPACITY;
+    LocateLaunch L;
+    memset(&L, 0, sizeof L);
+    fill_ref_table(refs, n_refs, 0, &L.refs);
+    L.n_refs = n_refs;
+    L.width = width;
+    L.q_ref = q_ref;
+    L.res = res;
+    L.n_q = n_q;
+    L.cap = cap;
+    L.out_offsets = out_offsets;
+    L.out_pos = out_pos;
+    L.capacity = out_pos ? out_pos_capacity : 0;
+    L.partials = partials;
+    return status_from_cuda(launch_locate(L, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 int sa_save(const sa_index *idx, const char *path, void *stream) {
     if (!idx || !path) return SA_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

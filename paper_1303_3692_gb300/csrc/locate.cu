@@ -7,7 +7,15 @@
 // CTA per tile that scans its own k_q, writes the offsets and gathers.  Each
 // tile is kTileThreads x kItems consecutive queries; a thread owns kItems
 // consecutive queries.
+#include <mutex>
+
 #include "sa_internal.cuh"
+
+// Scratch of sa_locate_noalloc: one partial sum per 4096-query tile of the
+// largest accepted batch, plus the total (131,080 bytes).  Every device that
+// loads the library holds it until exit.  Host code must pass its device
+// address (from cudaGetSymbolAddress), never the symbol itself.
+static __device__ __align__(256) uint64_t g_noalloc_partials[SA_LOCATE_NOALLOC_MAX_QUERIES / 4096 + 1];
 
 namespace sa {
 
@@ -122,6 +130,28 @@ __global__ void __launch_bounds__(kTileThreads) tile_gather_kernel(const __grid_
 }  // namespace
 
 uint64_t locate_tiles(uint64_t n_q) { return (n_q + kTile - 1) / kTile; }
+
+static_assert(kTile == 4096, "the static scratch below is sized for 4096-query tiles");
+
+cudaError_t locate_static_partials(uint64_t **ptr, uint64_t *entries) {
+    static std::mutex mu;
+    static uint64_t *addr[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess) return e;
+        addr[dev] = reinterpret_cast<uint64_t *>(p);
+    }
+    *ptr = addr[dev];
+    *entries = SA_LOCATE_NOALLOC_MAX_QUERIES / 4096 + 1;
+    return cudaSuccess;
+}
+
 
 cudaError_t launch_locate(const LocateLaunch &L, cudaStream_t s) {
     const uint64_t tiles = locate_tiles(L.n_q);

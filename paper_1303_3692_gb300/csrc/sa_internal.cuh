@@ -177,6 +177,9 @@ struct LocateLaunch {
     uint64_t *partials;       // scratch: one entry per scan tile + 1
 };
 uint64_t locate_tiles(uint64_t n_q);
+// Device address of the static scratch of sa_locate_noalloc on the current
+// device (looked up once per device) and the number of partial sums it holds.
+cudaError_t locate_static_partials(uint64_t **ptr, uint64_t *entries);
 cudaError_t launch_locate(const LocateLaunch &L, cudaStream_t s);
 
 }  // namespace sa

@@ -33,6 +33,7 @@ SA_ERR_IO = -7
 SA_ERR_FORMAT = -8
 SA_W32 = 0x1
 SA_W64 = 0x2
+SA_LOCATE_NOALLOC_MAX_QUERIES = 1 << 26
 
 _u64 = ctypes.c_uint64
 _u32 = ctypes.c_uint32
@@ -62,6 +63,7 @@ SIGNATURES = {
                                           ctypes.POINTER(sa_search_params)]),
     "sa_search_batch_plain": (ctypes.c_int, [ctypes.POINTER(_vp), _u32, _vp, _vp, _vp, _u64, _vp, _vp]),
     "sa_locate": (ctypes.c_int, [ctypes.POINTER(_vp), _u32, _vp, _vp, _u64, _u32, _vp, _vp, _u64, _vp]),
+    "sa_locate_noalloc": (ctypes.c_int, [ctypes.POINTER(_vp), _u32, _vp, _vp, _u64, _u32, _vp, _vp, _u64, _vp]),
     "sa_save": (ctypes.c_int, [_vp, ctypes.c_char_p, _vp]),
     "sa_load": (ctypes.c_int, [ctypes.c_char_p, _vp, ctypes.POINTER(_vp)]),
     "sa_index_info": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u32), ctypes.POINTER(_u32),
