@@ -117,7 +117,7 @@ int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_inde
  *             query whose range is inconsistent with them is reported like a
  *             non-ACGT byte.
  *  q_ref      n_q reference ids (< n_refs), or NULL when n_refs == 1.
- *  n_q        number of queries (0 is allowed and does nothing).
+ *  n_q        number of queries, < 2^32 (0 is allowed and does nothing).
  *  out        n_q results (host or device).
  *  stream     CUDA stream or NULL.
  *

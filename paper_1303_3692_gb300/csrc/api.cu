@@ -183,7 +183,7 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     int st = check_refs(refs, n_refs, &width);
     if (st) return st;
     if (n_q == 0) return SA_OK;
-    if (!q_offsets || !out || (n_refs > 1 && !q_ref)) return SA_ERR_ARG;
+    if (!q_offsets || !out || (n_refs > 1 && !q_ref) || n_q >= (1ull << 32)) return SA_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // First and last offset: read directly, or with one small synchronous copy.
     uint64_t first = 0, last = 0;

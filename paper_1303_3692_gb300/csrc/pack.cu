@@ -59,9 +59,41 @@ cudaError_t launch_pack_text(const char *ascii, uint64_t n, uint64_t *words, uin
     return cudaGetLastError();
 }
 
-// One warp per query: each step packs 128 bases, 4 per lane; the 8 lanes of
-// an octet OR their bytes into one 32-base word, written by the octet's
-// first lane.  Query q's words start at ((q_off[q] - q_off[0]) >> 5) + q.
+// Packs 32 ASCII bases starting at byte s of a (nb <= 32 valid bytes; the
+// rest pack as A).  The common case reads nine aligned 32-bit words inside
+// [a, a + total) and aligns them with funnel shifts.
+__device__ __forceinline__ uint64_t pack_word(const uint8_t *__restrict__ a, uint64_t total, uint64_t s,
+                                              uint32_t nb, bool *ok) {
+    const uintptr_t lo_addr = ((uintptr_t)(a + s)) & ~(uintptr_t)3;
+    uint64_t word = 0;
+    if (nb == 32 && lo_addr >= (uintptr_t)a && lo_addr + 36 <= (uintptr_t)(a + total)) {
+        const uint32_t *p = reinterpret_cast<const uint32_t *>(lo_addr);
+        const uint32_t sh = (uint32_t)(((uintptr_t)(a + s)) & 3u) * 8u;
+        uint32_t v[9];
+#pragma unroll
+        for (int i = 0; i < 9; i++) v[i] = __ldg(p + i);
+#pragma unroll
+        for (int i = 0; i < 8; i++) word = (word << 8) | pack4(__funnelshift_r(v[i], v[i + 1], sh), ok);
+    } else {
+        for (uint32_t j = 0; j < 32; j++) {
+            uint32_t code = 0;
+            if (j < nb) {
+                code = base_code(a[s + j]);
+                if (code > 3) {
+                    *ok = false;
+                    code = 0;
+                }
+            }
+            word = (word << 2) | code;
+        }
+    }
+    return word;
+}
+
+// Each warp takes 32 consecutive queries (one per lane), scans their word
+// counts, and then packs one output word per lane per round: a round covers
+// 32 consecutive 32-base words of the batch, so the lanes read one
+// contiguous kilobyte.  Query q's words start at ((q_off[q] - q_off[0]) >> 5) + q.
 __global__ void pack_queries_kernel(const uint8_t *__restrict__ ascii, const uint64_t *__restrict__ q_off,
                                     uint64_t first, uint64_t total, uint64_t n_q, uint64_t *__restrict__ qwords,
                                     int *err_flag) {
@@ -69,32 +101,47 @@ __global__ void pack_queries_kernel(const uint8_t *__restrict__ ascii, const uin
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     bool ok = true;
-    for (uint64_t q = warp; q < n_q; q += nwarps) {
-        const uint64_t a = __ldg(q_off + q) - first;
-        const uint64_t e = __ldg(q_off + q + 1) - first;
-        if (a > e || e > total) {  // inconsistent offsets: reported, nothing read or written
-            ok = false;
-            continue;
-        }
-        const uint64_t m = e - a;
-        uint64_t *dst = qwords + (a >> 5) + q;
-        for (uint64_t base = 0; base < m; base += 128) {
-            const uint64_t b = a + base + 4u * lane;
-            uint32_t v = 0x41414141u;  // bases past the end pack as A (code 0)
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                if (b + k < e) {
-                    const uint32_t c = ascii[b + k];
-                    v = (v & ~(0xFFu << (8 * k))) | (c << (8 * k));
-                }
+    for (uint64_t q0 = warp * 32; q0 < n_q; q0 += nwarps * 32) {
+        const uint64_t q = q0 + lane;
+        uint64_t a = 0, e = 0;
+        uint32_t words = 0;
+        if (q < n_q) {
+            a = __ldg(q_off + q) - first;
+            e = __ldg(q_off + q + 1) - first;
+            if (a > e || e > total || e - a >= (1ull << 31)) {
+                ok = false;  // inconsistent offsets: reported, nothing read or written
+                a = e = 0;
+            } else {
+                words = (uint32_t)((e - a + 31) >> 5);
             }
-            const uint64_t part = (uint64_t)pack4(v, &ok) << (56u - 8u * (lane & 7u));
-            uint64_t word = part;
-            word |= __shfl_xor_sync(0xFFFFFFFFu, word, 1);
-            word |= __shfl_xor_sync(0xFFFFFFFFu, word, 2);
-            word |= __shfl_xor_sync(0xFFFFFFFFu, word, 4);
-            const uint64_t wi = (base >> 5) + (lane >> 3);
-            if ((lane & 7u) == 0 && wi * 32 < m) dst[wi] = word;
+        }
+        uint32_t incl = words;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= (unsigned)o) incl += y;
+        }
+        const uint32_t excl = incl - words;
+        const uint32_t W = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        for (uint32_t base = 0; base < W; base += 32) {
+            const uint32_t t = base + lane;
+            // owner: the last lane whose first word is <= t
+            uint32_t i = 0;
+#pragma unroll
+            for (uint32_t b = 16; b > 0; b >>= 1) {
+                const uint32_t ex = __shfl_sync(0xFFFFFFFFu, excl, i + b);
+                if (ex <= t) i += b;
+            }
+            const uint64_t ai = __shfl_sync(0xFFFFFFFFu, a, i);
+            const uint64_t ei = __shfl_sync(0xFFFFFFFFu, e, i);
+            const uint32_t exi = __shfl_sync(0xFFFFFFFFu, excl, i);
+            if (t < W) {
+                const uint32_t j = t - exi;
+                const uint64_t s = ai + 32ull * j;
+                const uint64_t left = ei - s;
+                const uint32_t nb = left < 32 ? (uint32_t)left : 32u;
+                qwords[(ai >> 5) + q0 + i + j] = pack_word(ascii, total, s, nb, &ok);
+            }
         }
     }
     if (__any_sync(0xFFFFFFFFu, !ok) && lane == 0) atomicOr(err_flag, 1);
@@ -103,8 +150,8 @@ __global__ void pack_queries_kernel(const uint8_t *__restrict__ ascii, const uin
 cudaError_t launch_pack_queries(const char *ascii, const uint64_t *q_off, uint64_t first, uint64_t total,
                                 uint64_t n_q, uint64_t *qwords, int *err_flag, cudaStream_t s) {
     const int threads = 256;
-    const uint64_t warps_needed = n_q;
-    const uint64_t cap = (uint64_t)device_sm_count() * 64;  // 8 blocks x 8 warps per SM
+    const uint64_t warps_needed = (n_q + 31) / 32;
+    const uint64_t cap = (uint64_t)device_sm_count() * 16;  // 16 blocks x 8 warps per SM
     uint64_t blocks = (warps_needed + 7) / 8;
     if (blocks > cap) blocks = cap;
     if (blocks == 0) blocks = 1;

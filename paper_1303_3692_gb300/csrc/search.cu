@@ -88,12 +88,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 __host__ __device__ __forceinline__ uint32_t table_key_bytes(uint32_t d) { return 16u << d; }
 __host__ __device__ __forceinline__ uint32_t table_len_bytes(uint32_t d) { return d >= 4 ? (1u << d) : 16u; }
 
-// Rank sampled by level-order node k at level l: floor((2p + 1) n / 2^(l+1)).
-__device__ __forceinline__ int64_t node_rank(uint32_t k, uint32_t l, uint64_t n) {
-    const uint64_t p = k - (1u << l);
-    return (int64_t)(((2 * p + 1) * n) >> (l + 1));
-}
-
 // P's first 64 bases (q0, q1) against a 64-base key of length klen.  Sets
 // *undecided when both agree on 64 bases, m > 64 and the key has 64 bases.
 __device__ __forceinline__ int cmp_key(uint64_t q0, uint64_t q1, uint32_t m, uint4 kv, uint32_t klen,
@@ -136,60 +130,6 @@ __device__ __forceinline__ int cmp_key(uint64_t q0, uint64_t q1, uint32_t m, uin
     return CMP_PREFIX;
 }
 
-// Per-lane search state.  Phase 0: both bounds share (L, R).  Phase 1: the
-// lower bound in (L, R] after a split, with the upper bound's interval kept
-// in (HL, HR).  Phase 2: the upper bound.
-struct Lane {
-    int64_t L, R, HL, HR;
-    uint32_t lcpL, lcpR, hlcpL, hlcpR;
-    uint64_t lo;
-    int phase;
-};
-
-// Applies one compare outcome at pivot M.  In phase 0 a prefix match splits
-// the bounds; in phase 1 a prefix moves R (lower bound); in phase 2 it moves L.
-__device__ __forceinline__ void apply(Lane &s, int c, int64_t M, uint32_t l, uint32_t m) {
-    if (c == CMP_PREFIX && s.phase == 0) {
-        s.HL = M;
-        s.hlcpL = m;
-        s.HR = s.R;
-        s.hlcpR = s.lcpR;
-        s.R = M;
-        s.lcpR = m;
-        s.phase = 1;
-    } else if (c == CMP_LESS || (c == CMP_PREFIX && s.phase == 1)) {
-        s.R = M;
-        s.lcpR = l;
-    } else {
-        s.L = M;
-        s.lcpL = l;
-    }
-}
-
-// Moves through finished phases; returns true when the query is done, with
-// its interval in (*lo, *hi).
-__device__ __forceinline__ bool resolve(Lane &s, uint64_t *lo, uint64_t *hi) {
-    for (;;) {
-        if (s.R - s.L > 1) return false;
-        if (s.phase == 0) {
-            *lo = *hi = (uint64_t)s.R;
-            return true;
-        }
-        if (s.phase == 1) {
-            s.lo = (uint64_t)s.R;
-            s.L = s.HL;
-            s.R = s.HR;
-            s.lcpL = s.hlcpL;
-            s.lcpR = s.hlcpR;
-            s.phase = 2;
-            continue;
-        }
-        *lo = s.lo;
-        *hi = (uint64_t)s.R;
-        return true;
-    }
-}
-
 __device__ __forceinline__ void write_result(sa_result *out, uint64_t q, uint64_t lo, uint64_t hi) {
     sa_result r;
     r.lo = lo;
@@ -200,7 +140,50 @@ __device__ __forceinline__ void write_result(sa_result *out, uint64_t q, uint64_
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s for the key-table copy
 
-template <typename IdxT>
+// 32-bit form of cmp_query_suffix for texts of n < 2^32 bases: the suffix at
+// p has n - p >= 1 bases; the compare starts at the 32-aligned base below
+// `start` (< m).
+__device__ __forceinline__ int cmp_suffix32(const uint64_t *__restrict__ T, uint32_t n, uint32_t p,
+                                            const uint64_t *__restrict__ Q, uint32_t m, uint32_t start,
+                                            uint32_t *lcp) {
+    uint32_t off = start & ~31u;
+    const uint32_t rem = n - p;
+    for (;;) {
+        const uint32_t qlen = min(32u, m - off);
+        const uint32_t tlen = off < rem ? min(32u, rem - off) : 0u;
+        const uint64_t q = __ldg(Q + (off >> 5));
+        const uint64_t t = tlen ? text_window(T, (uint64_t)(p + off)) : 0ull;
+        const uint64_t x = q ^ t;
+        const uint32_t d = x ? ((uint32_t)__clzll((long long)x) >> 1) : 32u;
+        if (d < min(qlen, tlen)) {
+            *lcp = off + d;
+            return q < t ? CMP_LESS : CMP_GREATER;
+        }
+        if (tlen < qlen) {
+            *lcp = off + tlen;
+            return CMP_GREATER;
+        }
+        if (off + 32u >= m) {
+            *lcp = m;
+            return CMP_PREFIX;
+        }
+        off += 32u;
+    }
+}
+
+// The search of one query is a sequence of steps, one compare each, run by
+// its lane one step per loop iteration so that the 32 lanes of a warp stay in
+// the same short code path:
+//   init      read the query's offsets and first 64 bases;
+//   descent   compare with the key of level-order node k in shared memory
+//             (k = 0 once the table's depth is passed or the bounds split);
+//   deep      load SA[M] for M = L + (R - L)/2 and compare with the text.
+// Ranks are 32-bit modular: L = 0xFFFFFFFF stands for -1, and since every
+// rank is in [-1, n] with n < 2^32 - 1, R - L and L + (R - L)/2 are exact.
+// phase 0: both bounds share (L, R); a prefix match splits them into the
+// lower bound in (L, M] (phase 1) and the upper bound in [M, R), kept in
+// (HL, HR) until phase 1 ends (phase 2).
+template <typename IdxT, bool kSingle>
 __global__ void __launch_bounds__(1024, 1) search_kernel(const __grid_constant__ SearchLaunch a) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ SmemDesc sdesc[SA_MAX_REFS];
@@ -241,16 +224,22 @@ __global__ void __launch_bounds__(1024, 1) search_kernel(const __grid_constant__
     const unsigned lanemask_lt = (1u << lane) - 1u;
     const bool bad_batch = a.pack_err != nullptr && *(volatile const int *)a.pack_err != 0;
 
+    // Reference fields: uniform registers for one reference, else per lane.
+    const SmemDesc d0 = sdesc[0];
+    const uint64_t *T = d0.text;
+    const void *SAp = d0.sa;
+    uint32_t n = (uint32_t)d0.n;
+    const uint8_t *Ktab = smem + d0.off;
+    uint32_t depth = d0.depth;
+
     uint64_t pool_next = 0, pool_end = 0;  // warp-uniform chunk of query ids
     bool exhausted = false;
     bool active = false, fresh = false;
-    uint64_t q = 0;
+    uint32_t q = 0, m = 0;
     const uint64_t *Q = nullptr;
-    const uint64_t *T = nullptr;
-    const void *SAp = nullptr;
-    uint64_t n = 0;
-    uint32_t m = 0;
-    Lane s{};
+    uint64_t q0 = 0, q1 = 0;
+    uint32_t L = 0, R = 0, HL = 0, HR = 0, lcpL = 0, lcpR = 0, hlcpL = 0, hlcpR = 0, lo = 0;
+    uint32_t k = 0, phase = 0;
 
     for (;;) {
         unsigned need = __ballot_sync(0xFFFFFFFFu, !active);
@@ -270,7 +259,7 @@ __global__ void __launch_bounds__(1024, 1) search_kernel(const __grid_constant__
             const uint32_t avail = left < 32ull ? (uint32_t)left : 32u;
             const uint32_t rank = __popc(need & lanemask_lt);
             if (((need >> lane) & 1u) && rank < avail) {
-                q = pool_next + rank;
+                q = (uint32_t)(pool_next + rank);
                 active = true;
                 fresh = true;
             }
@@ -280,103 +269,91 @@ __global__ void __launch_bounds__(1024, 1) search_kernel(const __grid_constant__
         if (__ballot_sync(0xFFFFFFFFu, active) == 0u) break;
         if (!active) continue;
 
-        bool done = false;
-        uint64_t lo = 0, hi = 0;
         if (fresh) {
             fresh = false;
             const uint64_t a0 = __ldg(a.q_off + q) - a.first;
             const uint64_t a1 = __ldg(a.q_off + q + 1) - a.first;
-            const uint32_t r = a.q_ref ? __ldg(a.q_ref + q) : 0u;
+            const uint32_t r = (!kSingle && a.q_ref) ? __ldg(a.q_ref + q) : 0u;
             if (bad_batch || r >= a.n_refs || a1 < a0 || a1 > a.total || a1 - a0 >= (1ull << 31)) {
-                lo = hi = ~0ull;
-                done = true;
-            } else {
-                m = (uint32_t)(a1 - a0);
-                Q = a.qwords + (a0 >> 5) + q;
+                write_result(a.out, q, ~0ull, ~0ull);
+                active = false;
+                continue;
+            }
+            if (!kSingle) {
                 const SmemDesc d = sdesc[r];
                 T = d.text;
                 SAp = d.sa;
-                n = d.n;
-                s.L = -1;
-                s.R = (int64_t)n;
-                s.lcpL = s.lcpR = 0;
-                s.phase = 0;
-                if (m == 0) {
-                    lo = 0;
-                    hi = n;
-                    done = true;
-                } else if (d.depth) {
-                    // Top levels: walk the key table in shared memory.
-                    const uint4 *K = reinterpret_cast<const uint4 *>(smem + d.off);
-                    const uint8_t *KL = smem + d.off + table_key_bytes(d.depth);
-                    const uint64_t q0 = __ldg(Q);
-                    const uint64_t q1 = m > 32 ? __ldg(Q + 1) : 0ull;
-                    uint32_t k = 1, klo = 0, khi = 0;
-                    uint32_t lvl = 0;
-                    // lockstep until a split
-                    for (; lvl < d.depth; lvl++) {
-                        const int64_t M = node_rank(k, lvl, n);
-                        uint32_t l;
-                        bool und = false;
-                        int c = cmp_key(q0, q1, m, K[k], KL[k], &l, &und);
-                        if (und) c = cmp_query_suffix(T, n, sa_at<IdxT>(SAp, (uint64_t)M), Q, m, 64, &l);
-                        apply(s, c, M, l, m);
-                        if (s.phase) {
-                            klo = 2 * k;
-                            khi = 2 * k + 1;
-                            lvl++;
-                            break;
-                        }
-                        k = c == CMP_LESS ? 2 * k : 2 * k + 1;
-                    }
-                    if (s.phase) {
-                        // lower bound in the left subtree, then upper bound in the right one
-                        for (uint32_t l2 = lvl; l2 < d.depth; l2++) {
-                            const int64_t M = node_rank(klo, l2, n);
-                            uint32_t l;
-                            bool und = false;
-                            int c = cmp_key(q0, q1, m, K[klo], KL[klo], &l, &und);
-                            if (und) c = cmp_query_suffix(T, n, sa_at<IdxT>(SAp, (uint64_t)M), Q, m, 64, &l);
-                            apply(s, c, M, l, m);
-                            klo = c <= 0 ? 2 * klo : 2 * klo + 1;
-                        }
-                        Lane h = s;
-                        h.L = s.HL;
-                        h.R = s.HR;
-                        h.lcpL = s.hlcpL;
-                        h.lcpR = s.hlcpR;
-                        h.phase = 2;
-                        for (uint32_t l2 = lvl; l2 < d.depth; l2++) {
-                            const int64_t M = node_rank(khi, l2, n);
-                            uint32_t l;
-                            bool und = false;
-                            int c = cmp_key(q0, q1, m, K[khi], KL[khi], &l, &und);
-                            if (und) c = cmp_query_suffix(T, n, sa_at<IdxT>(SAp, (uint64_t)M), Q, m, 64, &l);
-                            apply(h, c, M, l, m);
-                            khi = c < 0 ? 2 * khi : 2 * khi + 1;
-                        }
-                        s.HL = h.L;
-                        s.HR = h.R;
-                        s.hlcpL = h.lcpL;
-                        s.hlcpR = h.lcpR;
-                    }
-                    done = resolve(s, &lo, &hi);
-                } else {
-                    done = resolve(s, &lo, &hi);
-                }
+                n = (uint32_t)d.n;
+                Ktab = smem + d.off;
+                depth = d.depth;
             }
-        } else {
-            // One deep probe: the suffix-array entry, then the text it points to.
-            const int64_t M = (s.L + s.R) >> 1;
-            const uint64_t p = sa_at<IdxT>(SAp, (uint64_t)M);
-            uint32_t l;
-            const int c = cmp_query_suffix(T, n, p, Q, m, min(s.lcpL, s.lcpR), &l);
-            apply(s, c, M, l, m);
-            done = resolve(s, &lo, &hi);
+            m = (uint32_t)(a1 - a0);
+            if (m == 0) {
+                write_result(a.out, q, 0, n);
+                active = false;
+                continue;
+            }
+            Q = a.qwords + (a0 >> 5) + q;
+            q0 = __ldg(Q);
+            q1 = m > 32 ? __ldg(Q + 1) : 0ull;
+            L = 0xFFFFFFFFu;
+            R = n;
+            lcpL = lcpR = 0;
+            phase = 0;
+            k = depth ? 1u : 0u;
         }
-        if (done) {
-            write_result(a.out, q, lo, hi);
-            active = false;
+
+        int c;
+        uint32_t l, M;
+        if (k != 0) {
+            // Descent: node k at level lvl samples rank floor((2p+1) n / 2^(lvl+1)).
+            const uint32_t lvl = 31u - __clz(k);
+            const uint32_t p = k - (1u << lvl);
+            M = __umulhi(n, (2u * p + 1u) << (31u - lvl));
+            const uint4 kv = reinterpret_cast<const uint4 *>(Ktab)[k];
+            const uint32_t klen = Ktab[(16u << depth) + k];
+            bool und = false;
+            c = cmp_key(q0, q1, m, kv, klen, &l, &und);
+            if (und) c = cmp_suffix32(T, n, (uint32_t)sa_at<IdxT>(SAp, M), Q, m, 64u, &l);
+            const uint32_t nk = 2u * k + (c == CMP_GREATER ? 1u : 0u);
+            k = (c == CMP_PREFIX || nk >= (1u << depth)) ? 0u : nk;
+        } else {
+            M = L + ((R - L) >> 1);
+            const uint32_t p = (uint32_t)sa_at<IdxT>(SAp, M);
+            c = cmp_suffix32(T, n, p, Q, m, min(lcpL, lcpR), &l);
+        }
+        if (c == CMP_PREFIX && phase == 0) {
+            HL = M;
+            hlcpL = m;
+            HR = R;
+            hlcpR = lcpR;
+            R = M;
+            lcpR = m;
+            phase = 1;
+            k = 0;
+        } else if (c == CMP_LESS || (c == CMP_PREFIX && phase == 1)) {
+            R = M;
+            lcpR = l;
+        } else {
+            L = M;
+            lcpL = l;
+        }
+        // Finished intervals: move to the upper bound, or write the result.
+        if (R - L <= 1u) {
+            if (phase == 1) {
+                lo = R;
+                L = HL;
+                R = HR;
+                lcpL = hlcpL;
+                lcpR = hlcpR;
+                phase = 2;
+                k = 0;
+            }
+            if (R - L <= 1u) {
+                const uint32_t lo_out = phase == 0 ? R : lo;
+                write_result(a.out, q, lo_out, R);
+                active = false;
+            }
         }
     }
 }
@@ -440,13 +417,15 @@ __global__ void __launch_bounds__(256) search_plain_kernel(const __grid_constant
 cudaError_t launch_search(const SearchLaunch &L, cudaStream_t s) {
     if (L.n_q == 0) return cudaSuccess;
     const size_t smem = L.smem_bytes;
-    if (L.width == 4) {
-        cudaFuncSetAttribute(search_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        search_kernel<uint32_t><<<L.blocks, L.threads, smem, s>>>(L);
-    } else {
-        cudaFuncSetAttribute(search_kernel<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        search_kernel<uint64_t><<<L.blocks, L.threads, smem, s>>>(L);
-    }
+    const bool single = L.n_refs == 1 && L.q_ref == nullptr;
+    auto go = [&](auto kernel) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kernel<<<L.blocks, L.threads, smem, s>>>(L);
+    };
+    if (L.width == 4)
+        single ? go(search_kernel<uint32_t, true>) : go(search_kernel<uint32_t, false>);
+    else
+        single ? go(search_kernel<uint64_t, true>) : go(search_kernel<uint64_t, false>);
     return cudaGetLastError();
 }
 
