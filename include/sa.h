@@ -56,8 +56,11 @@ extern "C" {
 #define SA_ERR_FORMAT -8   /* file is not an index, or its checksum does not match */
 
 /* sa_build flags. */
-#define SA_W32 0x1u /* store the suffix array as uint32 (n < 2^32 - 1) */
-#define SA_W64 0x2u /* store the suffix array as uint64 */
+#define SA_W32 0x1u     /* store the suffix array as uint32 (n < 2^32 - 1) */
+#define SA_W64 0x2u     /* store the suffix array as uint64 */
+#define SA_NO_KMER 0x4u /* build no k-mer table (see sa_build) */
+/* k of the k-mer table, 1..15, in bits 8-11; 0 there picks k automatically. */
+#define SA_KMER_K(k) ((uint32_t)(k) << 8)
 
 /* Opaque index: 2-bit packed reference, its suffix array and its sampled-key
  * table, resident in device memory. */
@@ -79,8 +82,17 @@ typedef struct sa_search_params {
     uint32_t chunk;             /* queries a warp takes from the global counter at once */
     void *search_events[2];     /* optional cudaEvent_t pair, recorded on the stream right
                                    before and after the search kernel (kernel timing) */
+    uint32_t flags;             /* SA_PARAM_Q_RANGE: q_first and q_total are given */
+    uint32_t reserved0;
+    uint64_t q_first;           /* q_offsets[0] */
+    uint64_t q_total;           /* q_offsets[n_q] - q_offsets[0] */
     uint32_t reserved[4];
 } sa_search_params;
+
+/* sa_search_params.flags: the caller states q_offsets[0] and the batch's
+ * total bases, so a call with device-resident offsets reads nothing back to
+ * the host and does not synchronize. */
+#define SA_PARAM_Q_RANGE 0x1u
 
 /*
  * sa_build -- index one reference (Section III).
@@ -88,12 +100,23 @@ typedef struct sa_search_params {
  * Packs the bases 2 bits each (A=0, C=1, G=2, T=3, base 0 in the most
  * significant bits of each 64-bit word), builds the suffix array of the text
  * on the GPU by prefix doubling (radix sorts of rank pairs; the result is the
- * unique suffix array of Table I's definition), and samples the key table
- * that the search keeps in shared memory.
+ * unique suffix array of Table I's definition), and derives the structures
+ * the search reads:
+ *  - the key table kept in shared memory (first 64 bases of the suffixes at
+ *    ranks floor((2p+1) n / 2^(l+1)), the top levels of the binary search);
+ *  - one 16-byte record per rank (the first 48 bases of that suffix and its
+ *    position), so that a probe reads one aligned record;
+ *  - unless SA_NO_KMER, the k-mer table kmer[x] = number of suffixes that
+ *    sort before the k-base string x, for all 4^k strings (+1 entry = n);
+ *    a query of m >= k bases whose first k bases are x lies strictly between
+ *    ranks kmer[x] - 1 and kmer[x + 1].  Automatic k: the largest k with
+ *    4^k <= 4n, in 1..15 (4^k * 4 bytes: 1 GB at k = 14 for 10^8 bases).
+ * Device memory: about n/4 + (width + 32) n bytes + the k-mer table.
  *
  *  text   n bytes of bases, host or device memory.
  *  n      number of bases, 1 <= n < 2^32 - 1.
- *  flags  SA_W32 or SA_W64 (exactly one): element width of the suffix array.
+ *  flags  SA_W32 or SA_W64 (exactly one): element width of the suffix array;
+ *         optionally SA_NO_KMER or SA_KMER_K(k).
  *  stream CUDA stream (cudaStream_t) or NULL.
  *  out    receives the new index.
  *
@@ -113,8 +136,9 @@ int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_inde
  *  q_offsets  n_q + 1 uint64 offsets into q_bases, non-decreasing, q_offsets[0]
  *             may be non-zero; query i is q_bases[q_offsets[i] .. q_offsets[i+1]).
  *             Only the first and last entry are read on the host (with one
- *             small synchronous copy when the array is in device memory); a
- *             query whose range is inconsistent with them is reported like a
+ *             small synchronous copy when the array is in device memory,
+ *             unless sa_search_batch_ex is given SA_PARAM_Q_RANGE); a query
+ *             whose range is inconsistent with them is reported like a
  *             non-ACGT byte.
  *  q_ref      n_q reference ids (< n_refs), or NULL when n_refs == 1.
  *  n_q        number of queries, < 2^32 (0 is allowed and does nothing).
@@ -213,9 +237,14 @@ int sa_save(const sa_index *idx, const char *path, void *stream);
  * SA_ERR_IO, SA_ERR_FORMAT (bad magic, version or checksum), SA_ERR_NOMEM. */
 int sa_load(const char *path, void *stream, sa_index **out);
 
-/* Size facts of an index; any output pointer may be NULL. */
+/* Size facts of an index; any output pointer may be NULL.  kmer_k is 0 when
+ * the index has no k-mer table. */
 int sa_index_info(const sa_index *idx, uint64_t *n, uint32_t *width, uint32_t *key_depth,
-                  uint64_t *device_bytes);
+                  uint32_t *kmer_k, uint64_t *device_bytes);
+
+/* Copies the k-mer table (4^k + 1 uint32) to dst (host or device).
+ * SA_ERR_ARG if the index has none. */
+int sa_copy_kmer_table(const sa_index *idx, void *dst, void *stream);
 
 /* Copies the suffix array (n elements of the index's width) to dst (host or
  * device).  Asynchronous on stream for device/pinned dst. */

@@ -66,6 +66,11 @@ def _load():
         lib.oracle_probe_model.argtypes = [_p, _i64, _p, _p, _i64, ctypes.c_int,
                                            _pi64, _pi64, _pi64, _pi64]
         lib.oracle_probe_model.restype = None
+        lib.oracle_kmer_table.argtypes = [_p, _i64, _p, ctypes.c_int, _p]
+        lib.oracle_kmer_table.restype = None
+        lib.oracle_probe_model_kmer.argtypes = [_p, _i64, _p, _p, ctypes.c_int, ctypes.c_int, _p, _i64,
+                                                _pi64, _pi64, _pi64, _pi64, _pi64]
+        lib.oracle_probe_model_kmer.restype = None
         _lib = lib
     return _lib
 
@@ -197,3 +202,24 @@ def probe_model(T, sa, P, d0: int = 13):
     _load().oracle_probe_model(_ptr(T), T.size, _ptr(sa), _ptr(P), P.size, int(d0),
                                ctypes.byref(pr), ctypes.byref(ch), ctypes.byref(lo), ctypes.byref(hi))
     return pr.value, ch.value, lo.value, hi.value
+
+
+def kmer_table(T, sa, k: int) -> np.ndarray:
+    """table[x] = number of suffixes sorting before the k-base string x; table[4^k] = n."""
+    T = _u8(T)
+    sa = np.ascontiguousarray(sa, dtype=np.int64)
+    out = np.empty((1 << (2 * k)) + 1, dtype=np.int64)
+    _load().oracle_kmer_table(_ptr(T), T.size, _ptr(sa), int(k), _ptr(out))
+    return out
+
+
+def probe_model_kmer(T, sa, table, k: int, P, d0: int = 13):
+    """(probes, text windows, table reads, lo, hi) of the k-mer + record search model."""
+    T, P = _u8(T), _u8(P)
+    sa = np.ascontiguousarray(sa, dtype=np.int64)
+    tab = None if table is None else np.ascontiguousarray(table, dtype=np.int64)
+    pr, wi, tr, lo, hi = _i64(), _i64(), _i64(), _i64(), _i64()
+    _load().oracle_probe_model_kmer(_ptr(T), T.size, _ptr(sa), None if tab is None else _ptr(tab), int(k), int(d0),
+                                    _ptr(P), P.size, ctypes.byref(pr), ctypes.byref(wi), ctypes.byref(tr),
+                                    ctypes.byref(lo), ctypes.byref(hi))
+    return pr.value, wi.value, tr.value, lo.value, hi.value

@@ -14,7 +14,16 @@ P_q counts the probes of the lockstep lower/upper-bound search at depth
 the 64-base chunks those probes compare, starting at min(lcp(P,S_L),
 lcp(P,S_R)).  Locate adds w * min(count, cap) written plus the same read.
 
-    python -m oracle.bytes_model --workload repetitive-100m [--sample 20000]
+The second figure models the search as the CUDA path runs it with a k-mer
+table and 32-byte suffix records of 112 bases (oracle_probe_model_kmer):
+
+    B_q = ceil(m/4) + 32 * [m >= k] + 32 * P'_q + 32 * W_q + 3 * w
+
+P'_q probes read one record sector each (below depth d0 only when no k-mer
+bracket applies), W_q counts the 32-base text windows of compares that tie on
+a record's 112 bases.
+
+    python -m oracle.bytes_model --workload repetitive-100m [--sample 20000] [--k 12]
 """
 from __future__ import annotations
 
@@ -37,16 +46,29 @@ WORKLOADS = {
 }
 
 
-def model(w, sample: int, d0: int, seed: int = 7):
+def auto_k(n: int) -> int:
+    """The largest k with 4^k <= 4n, in 1..15 (the library's automatic choice)."""
+    k = 1
+    while k < 15 and (1 << (2 * (k + 1))) <= 4 * n:
+        k += 1
+    return k
+
+
+def model(w, sample: int, d0: int, k: int = 0, seed: int = 7):
     T = oracle.normalize(w.ref)
     t0 = time.time()
     sa = oracle.sa_naive(T)
     build_s = time.time() - t0
+    k = k or auto_k(T.size)
+    t0 = time.time()
+    table = oracle.kmer_table(T, sa, k)
+    table_s = time.time() - t0
     n_q = w.q_offsets.size - 1
     rng = np.random.default_rng(seed)
     pick = np.sort(rng.choice(n_q, size=min(sample, n_q), replace=False))
     wbytes = 4 if w.width == 32 else 8
-    tot = {"query": 0, "sa": 0, "text": 0, "out": 0, "locate": 0, "probes": 0, "chunks": 0, "count": 0}
+    tot = {"query": 0, "sa": 0, "text": 0, "out": 0, "locate": 0, "probes": 0, "chunks": 0, "count": 0,
+           "k_table": 0, "k_probes": 0, "k_windows": 0}
     for q in pick:
         P = w.q_bases[w.q_offsets[q]:w.q_offsets[q + 1]]
         pr, ch, lo, hi = oracle.probe_model(T, sa, P, d0=d0)
@@ -56,15 +78,23 @@ def model(w, sample: int, d0: int, seed: int = 7):
         tot["out"] += 3 * wbytes
         tot["probes"] += pr
         tot["chunks"] += ch
-        k = min(hi - lo, w.cap)
         tot["count"] += hi - lo
-        tot["locate"] += 2 * wbytes * k
-    k = len(pick)
-    per = {key: v / k for key, v in tot.items()}
+        tot["locate"] += 2 * wbytes * min(hi - lo, w.cap)
+        kp, kw, kt, klo, khi = oracle.probe_model_kmer(T, sa, table, k, P, d0=d0)
+        assert (klo, khi) == (lo, hi)
+        tot["k_table"] += 32 * kt
+        tot["k_probes"] += kp
+        tot["k_windows"] += kw
+    cnt = len(pick)
+    per = {key: v / cnt for key, v in tot.items()}
     per["search_bytes_per_query"] = per["query"] + per["sa"] + per["text"] + per["out"]
-    per["sample"] = k
+    per["kmer_record_bytes_per_query"] = (per["query"] + per["k_table"] + 32 * per["k_probes"] +
+                                          32 * per["k_windows"] + per["out"])
+    per["k"] = k
+    per["sample"] = cnt
     per["d0"] = d0
     per["oracle_sa_build_s"] = build_s
+    per["oracle_kmer_table_s"] = table_s
     return per
 
 
@@ -73,9 +103,10 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="repetitive-100m")
     ap.add_argument("--sample", type=int, default=20000)
     ap.add_argument("--d0", type=int, default=13)
+    ap.add_argument("--k", type=int, default=0, help="k-mer table k (0: automatic)")
     a = ap.parse_args()
     w = WORKLOADS[a.workload]()
-    print(json.dumps({"workload": w.name, **model(w, a.sample, a.d0)}, indent=1))
+    print(json.dumps({"workload": w.name, **model(w, a.sample, a.d0, a.k)}, indent=1))
 
 
 if __name__ == "__main__":

@@ -483,3 +483,114 @@ void oracle_probe_model(const uint8_t *T, int64_t n, const int64_t *sa,
     }
     *hi = b;
 }
+
+/* ------------------------------------------------------------------ */
+/* k-mer table (an exact shortcut for the top of the binary search)    */
+/* ------------------------------------------------------------------ */
+
+/* Compares suffix S_p with the k-base string X: -1 if S_p sorts before X
+ * (including when S_p is a proper prefix of X), 0 if X is a prefix of S_p,
+ * +1 otherwise. */
+static int suffix_vs_string(const uint8_t *T, int64_t n, int64_t p, const uint8_t *X, int64_t k)
+{
+    for (int64_t t = 0; t < k; t++) {
+        if (p + t >= n)
+            return -1;
+        if (T[p + t] != X[t])
+            return T[p + t] < X[t] ? -1 : 1;
+    }
+    return 0;
+}
+
+/* table[x] = the number of suffixes that sort before the k-base string whose
+ * bases are the base-4 digits of x (A=0 C=1 G=2 T=3, most significant
+ * first), for x in [0, 4^k); table[4^k] = n.  Each entry is the lower bound
+ * of that string in the sorted suffixes (a binary search over sa). */
+void oracle_kmer_table(const uint8_t *T, int64_t n, const int64_t *sa, int k, int64_t *table)
+{
+    static const uint8_t letters[4] = {'A', 'C', 'G', 'T'};
+    uint8_t X[32];
+    int64_t count = (int64_t)1 << (2 * k);
+    for (int64_t x = 0; x < count; x++) {
+        for (int t = 0; t < k; t++)
+            X[t] = letters[(x >> (2 * (k - 1 - t))) & 3];
+        int64_t lo = 0, hi = n; /* first rank whose suffix is not before X */
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (suffix_vs_string(T, n, sa[mid], X, k) < 0)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        table[x] = lo;
+    }
+    table[count] = n;
+}
+
+/* Byte model of the search as the CUDA path runs it on an index with a k-mer
+ * table and 16-byte suffix records (measurement, not a parity output).
+ * A query of m >= k bases starts between ranks table[x] - 1 and table[x + 1]
+ * (x = its first k bases) and costs one table sector; shorter queries start
+ * at [-1, n) and their first d0 probes are free (shared-memory key table).
+ * Every other probe of the lockstep lower/upper-bound search reads one
+ * 32-byte record sector holding the suffix's first 112 bases; a compare that
+ * agrees on all 112 (m > 112, suffix >= 112 bases) also reads the 32-base
+ * text windows from base 96 up to the one where it is decided.  *probes,
+ * *windows count them; *table_reads is 1 or 0. */
+void oracle_probe_model_kmer(const uint8_t *T, int64_t n, const int64_t *sa, const int64_t *table, int k,
+                             int d0, const uint8_t *P, int64_t m, int64_t *probes, int64_t *windows,
+                             int64_t *table_reads, int64_t *lo_out, int64_t *hi_out)
+{
+    *probes = 0;
+    *windows = 0;
+    *table_reads = 0;
+    int64_t L = -1, R = n;
+    int depth = 0, free_levels = 0;
+    if (table && m >= k && k > 0) {
+        int64_t x = 0;
+        for (int t = 0; t < k; t++)
+            x = x * 4 + (P[t] == 'A' ? 0 : P[t] == 'C' ? 1 : P[t] == 'G' ? 2 : 3);
+        L = table[x] - 1;
+        R = table[x + 1];
+        *table_reads = 1;
+    } else {
+        free_levels = d0;
+    }
+    int phase = 0;
+    int64_t HL = 0, HR = 0, lo = 0;
+    for (;;) {
+        if (R - L <= 1) {
+            if (phase == 1) {
+                lo = R;
+                L = HL;
+                R = HR;
+                phase = 2;
+                continue;
+            }
+            *lo_out = phase == 0 ? R : lo;
+            *hi_out = R;
+            return;
+        }
+        int64_t M = (L + R) >> 1;
+        int64_t l;
+        int c = query_cmp(T, n, sa[M], P, m, &l);
+        if (depth >= free_levels) {
+            (*probes)++;
+            if (m > 112 && n - sa[M] >= 112 && l >= 112) {
+                int64_t last = l < m - 1 ? l : m - 1;
+                *windows += last / 32 - 3 + 1; /* windows from base 96 to the deciding one */
+            }
+        }
+        depth++;
+        if (c == 0 && phase == 0) {
+            HL = M;
+            HR = R;
+            R = M;
+            phase = 1;
+        } else if (c < 0 || (c == 0 && phase == 1)) {
+            R = M;
+        } else {
+            L = M;
+        }
+    }
+}

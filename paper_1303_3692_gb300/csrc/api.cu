@@ -144,7 +144,8 @@ int check_refs(const sa_index *const *refs, uint32_t n_refs, uint32_t *width) {
 
 // Per-index table depths for one call: each index's own depth, capped by the
 // request, then the deepest tables are trimmed until all fit the budget.
-uint32_t fill_ref_table(const sa_index *const *refs, uint32_t n_refs, uint32_t want_depth, RefTable *t) {
+uint32_t fill_ref_table(const sa_index *const *refs, uint32_t n_refs, uint32_t want_depth, RefTable *t,
+                        uint32_t budget = kSmemBudget) {
     uint32_t use[SA_MAX_REFS];
     for (uint32_t r = 0; r < n_refs; r++) {
         use[r] = refs[r]->depth < want_depth ? refs[r]->depth : want_depth;
@@ -155,7 +156,7 @@ uint32_t fill_ref_table(const sa_index *const *refs, uint32_t n_refs, uint32_t w
             total += search_table_bytes(use[r]);
             if (use[r] > use[deepest]) deepest = r;
         }
-        if (total <= kSmemBudget || use[deepest] == 0) break;
+        if (total <= budget || use[deepest] == 0) break;
         use[deepest]--;
     }
     uint32_t off = 0;
@@ -166,11 +167,13 @@ uint32_t fill_ref_table(const sa_index *const *refs, uint32_t n_refs, uint32_t w
         d.sa = x->sa;
         d.keys = x->keys;
         d.keylen = x->keylen;
+        d.rec = x->rec;
+        d.kmer = x->kmer;
+        d.kmer_k = x->kmer_k;
         d.n = x->n;
         d.depth = x->depth;
         d.use_depth = use[r];
         d.smem_off = off;
-        d.pad = 0;
         off += search_table_bytes(use[r]);
     }
     return off;
@@ -185,10 +188,13 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     if (n_q == 0) return SA_OK;
     if (!q_offsets || !out || (n_refs > 1 && !q_ref) || n_q >= (1ull << 32)) return SA_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    // First and last offset: read directly, or with one small synchronous copy.
+    // First and last offset: given, read directly, or with one small synchronous copy.
     uint64_t first = 0, last = 0;
     const bool off_dev = on_device(q_offsets);
-    if (off_dev) {
+    if (params && (params->flags & SA_PARAM_Q_RANGE)) {
+        first = params->q_first;
+        last = params->q_first + params->q_total;
+    } else if (off_dev) {
         uint64_t fl[2];
         cudaError_t e = cudaMemcpyAsync(&fl[0], q_offsets, 8, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&fl[1], q_offsets + n_q, 8, cudaMemcpyDeviceToHost, s);
@@ -221,8 +227,10 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     const uint32_t *ref_d = n_refs > 1 || q_ref ? device_view(q_ref, n_q, sc, &err) : nullptr;
     const bool out_dev = on_device(out);
     sa_result *out_d = out_dev ? out : sc.get<sa_result>(n_q);
-    const uint64_t nwords = (total >> 5) + n_q + 1;
-    uint64_t *qwords = sc.get<uint64_t>(nwords);
+    const uint64_t nslots = (total >> 7) + n_q + 1;
+    if (nslots >= (1ull << 32)) return SA_ERR_ARG;
+    uint64_t *qwords = sc.get<uint64_t>(4 * nslots);
+    uint4 *meta = sc.get<uint4>(n_q);
     int *flags = sc.get<int>(4);  // [0] pack error, [1] status
     unsigned long long *counter = sc.get<unsigned long long>(1);
     if (sc.failed) return SA_ERR_NOMEM;
@@ -233,8 +241,13 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
 
     SearchLaunch L;
     memset(&L, 0, sizeof L);
+    const uint32_t threads = params && params->threads_per_block ? params->threads_per_block : 1024;
+    const uint32_t bps = params && params->blocks_per_sm ? params->blocks_per_sm : 1;
+    if (threads < 32 || threads > 1024 || threads % 32 || bps == 0 || threads * bps > 2048) return SA_ERR_ARG;
+    // shared memory per SM is 228 KB; each CTA also holds ~3 KB of descriptors
+    const uint32_t budget = (kSmemBudget < 224u * 1024u / bps ? kSmemBudget : 224u * 1024u / bps) - 4096u;
     const uint32_t want_depth = params && params->key_depth ? params->key_depth : kDefaultDepth;
-    L.smem_bytes = fill_ref_table(refs, n_refs, plain ? 0 : want_depth, &L.refs);
+    L.smem_bytes = fill_ref_table(refs, n_refs, plain ? 0 : want_depth, &L.refs, budget);
     L.n_refs = n_refs;
     L.width = width;
     L.ascii = bases_d;
@@ -244,19 +257,17 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     L.total = total;
     L.q_ref = ref_d;
     L.n_q = n_q;
+    L.meta = meta;
     L.out = out_d;
     L.pack_err = flags;
     L.counter = counter;
     L.status = flags + 1;
     const int sms = device_sm_count();
-    L.threads = params && params->threads_per_block ? params->threads_per_block : 1024;
-    if (L.threads < 32 || L.threads > 1024 || L.threads % 32) return SA_ERR_ARG;
-    const uint32_t bps = params && params->blocks_per_sm ? params->blocks_per_sm : 1;
+    L.threads = threads;
     L.blocks = (uint32_t)sms * bps;
     L.chunk = params && params->chunk ? params->chunk : 64;
 
-    if (total > 0 && (err = launch_pack_queries(bases_d, off_d, first, total, n_q, qwords, flags, s)) != cudaSuccess)
-        return status_from_cuda(err);
+    if ((err = launch_pack_queries(L, flags, s)) != cudaSuccess) return status_from_cuda(err);
     cudaEvent_t ev0 = params ? reinterpret_cast<cudaEvent_t>(params->search_events[0]) : nullptr;
     cudaEvent_t ev1 = params ? reinterpret_cast<cudaEvent_t>(params->search_events[1]) : nullptr;
     if (ev0 && (err = cudaEventRecord(ev0, s)) != cudaSuccess) return status_from_cuda(err);
@@ -284,10 +295,20 @@ void free_index(sa_index *idx) {
     if (idx->sa) cudaFree(idx->sa);
     if (idx->keys) cudaFree(idx->keys);
     if (idx->keylen) cudaFree(idx->keylen);
+    if (idx->rec) cudaFree(idx->rec);
+    if (idx->kmer) cudaFree(idx->kmer);
     delete idx;
 }
 
 uint32_t table_entries(uint32_t depth) { return depth >= 4 ? (1u << depth) : 16u; }
+
+// Automatic k: the largest k with 4^k <= 4n, in 1..15 (one suffix per two to
+// eight k-mers; the table is at most 16n bytes, half the records' size).
+uint32_t auto_kmer_k(uint64_t n) {
+    uint32_t k = 1;
+    while (k < 15 && (1ull << (2 * (k + 1))) <= 4 * n) k++;
+    return k;
+}
 
 // Allocates the device arrays of an index whose n, width and depth are set.
 int alloc_index(sa_index *idx) {
@@ -296,12 +317,22 @@ int alloc_index(sa_index *idx) {
     const size_t sb = idx->n * (size_t)idx->width;
     const size_t kb = table_entries(idx->depth) * sizeof(uint4);
     const size_t lb = table_entries(idx->depth);
+    const size_t rb = idx->n * 2 * sizeof(uint4);
     if (cudaMalloc(&idx->text, tb) != cudaSuccess || cudaMalloc(&idx->sa, sb) != cudaSuccess ||
-        cudaMalloc(&idx->keys, kb) != cudaSuccess || cudaMalloc(&idx->keylen, lb) != cudaSuccess) {
+        cudaMalloc(&idx->keys, kb) != cudaSuccess || cudaMalloc(&idx->keylen, lb) != cudaSuccess ||
+        cudaMalloc(&idx->rec, rb) != cudaSuccess) {
         cudaGetLastError();
         return SA_ERR_NOMEM;
     }
-    idx->device_bytes = tb + sb + kb + lb;
+    size_t mb = 0;
+    if (idx->kmer_k) {
+        mb = ((1ull << (2 * idx->kmer_k)) + 1) * sizeof(uint32_t);
+        if (cudaMalloc(&idx->kmer, mb) != cudaSuccess) {
+            cudaGetLastError();
+            return SA_ERR_NOMEM;
+        }
+    }
+    idx->device_bytes = tb + sb + kb + lb + rb + mb;
     return SA_OK;
 }
 
@@ -318,7 +349,7 @@ struct FileHeader {
     char magic[8];
     uint32_t version, width;
     uint64_t n;
-    uint32_t depth, pad;
+    uint32_t depth, kmer_k;
     uint64_t nwords;
     uint64_t checksum;
 };
@@ -338,7 +369,8 @@ int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_inde
     if (!text || n == 0 || n >= 0xFFFFFFFFull) return SA_ERR_ARG;
     const uint32_t wflags = flags & (SA_W32 | SA_W64);
     if (wflags != SA_W32 && wflags != SA_W64) return SA_ERR_ARG;
-    if (flags & ~(SA_W32 | SA_W64)) return SA_ERR_ARG;
+    if (flags & ~(SA_W32 | SA_W64 | SA_NO_KMER | SA_KMER_K(15))) return SA_ERR_ARG;
+    const uint32_t want_k = (flags >> 8) & 15u;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     sa_index *idx = new (std::nothrow) sa_index();
     if (!idx) return SA_ERR_NOMEM;
@@ -350,6 +382,7 @@ int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_inde
     idx->width = wflags == SA_W32 ? 4 : 8;
     const uint32_t lg = floor_log2(n);
     idx->depth = lg < kDefaultDepth ? lg : kDefaultDepth;
+    idx->kmer_k = (flags & SA_NO_KMER) ? 0u : (want_k ? want_k : auto_kmer_k(n));
     int st = alloc_index(idx);
     if (st) {
         free_index(idx);
@@ -381,6 +414,8 @@ int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_inde
     st = build_suffix_array(idx, s);
     if (st == SA_OK) {
         cudaError_t err = launch_build_keys(idx, s);
+        if (err == cudaSuccess) err = launch_build_records(idx, s);
+        if (err == cudaSuccess) err = launch_build_kmer(idx, s);
         if (err == cudaSuccess) err = cudaStreamSynchronize(s);
         st = status_from_cuda(err);
     }
@@ -520,6 +555,7 @@ int sa_save(const sa_index *idx, const char *path, void *stream) {
     h.width = idx->width;
     h.n = idx->n;
     h.depth = idx->depth;
+    h.kmer_k = idx->kmer_k;
     h.nwords = idx->nwords;
     h.checksum = fnv1a(14695981039346656037ull, buf.data(), buf.size());
     FILE *f = fopen(path, "wb");
@@ -541,7 +577,7 @@ int sa_load(const char *path, void *stream, sa_index **out) {
         return SA_ERR_FORMAT;
     }
     if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 1 || (h.width != 4 && h.width != 8) || h.n == 0 ||
-        h.n >= 0xFFFFFFFFull || h.nwords != (h.n + 31) / 32 || h.depth > SA_MAX_KEY_DEPTH) {
+        h.n >= 0xFFFFFFFFull || h.nwords != (h.n + 31) / 32 || h.depth > SA_MAX_KEY_DEPTH || h.kmer_k > 15) {
         fclose(f);
         return SA_ERR_FORMAT;
     }
@@ -554,6 +590,7 @@ int sa_load(const char *path, void *stream, sa_index **out) {
     idx->n = h.n;
     idx->width = h.width;
     idx->depth = h.depth;
+    idx->kmer_k = h.kmer_k;
     const size_t tb = (h.nwords + SA_PAD_WORDS) * 8, sb = h.n * (size_t)h.width;
     const size_t kb = table_entries(h.depth) * sizeof(uint4), lb = table_entries(h.depth);
     std::vector<uint8_t> buf;
@@ -579,6 +616,8 @@ int sa_load(const char *path, void *stream, sa_index **out) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(idx->sa, buf.data() + tb, sb, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(idx->keys, buf.data() + tb + sb, kb, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(idx->keylen, buf.data() + tb + sb + kb, lb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_build_records(idx, s);
+    if (e == cudaSuccess) e = launch_build_kmer(idx, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         free_index(idx);
@@ -588,13 +627,22 @@ int sa_load(const char *path, void *stream, sa_index **out) {
     return SA_OK;
 }
 
-int sa_index_info(const sa_index *idx, uint64_t *n, uint32_t *width, uint32_t *key_depth, uint64_t *device_bytes) {
+int sa_index_info(const sa_index *idx, uint64_t *n, uint32_t *width, uint32_t *key_depth, uint32_t *kmer_k,
+                  uint64_t *device_bytes) {
     if (!idx) return SA_ERR_ARG;
     if (n) *n = idx->n;
     if (width) *width = idx->width;
     if (key_depth) *key_depth = idx->depth;
+    if (kmer_k) *kmer_k = idx->kmer_k;
     if (device_bytes) *device_bytes = idx->device_bytes;
     return SA_OK;
+}
+
+int sa_copy_kmer_table(const sa_index *idx, void *dst, void *stream) {
+    if (!idx || !dst || !idx->kmer) return SA_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t bytes = ((1ull << (2 * idx->kmer_k)) + 1) * sizeof(uint32_t);
+    return status_from_cuda(cudaMemcpyAsync(dst, idx->kmer, bytes, cudaMemcpyDefault, s));
 }
 
 int sa_copy_suffix_array(const sa_index *idx, void *dst, void *stream) {

@@ -244,4 +244,63 @@ cudaError_t launch_build_keys(sa_index *idx, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Suffix records: for rank i, the first 112 bases of suffix SA[i] and SA[i]
+// itself in one 32-byte entry (one DRAM sector), so that a probe of the
+// search reads one aligned sector instead of an SA entry and then the text it
+// points to, and a query of up to 112 bases never reads the text.
+template <typename IdxT>
+__global__ void build_records_kernel(const uint64_t *__restrict__ T, const IdxT *__restrict__ sa, uint64_t n,
+                                     uint4 *rec) {
+    GS_LOOP(i, n) {
+        const uint64_t pos = sa[i];
+        const uint64_t w0 = text_window(T, pos);
+        const uint64_t w1 = text_window(T, pos + 32);
+        const uint64_t w2 = text_window(T, pos + 64);
+        const uint64_t w3 = text_window(T, pos + 96);
+        rec[2 * i] = make_uint4((uint32_t)w0, (uint32_t)(w0 >> 32), (uint32_t)w1, (uint32_t)(w1 >> 32));
+        rec[2 * i + 1] = make_uint4((uint32_t)w2, (uint32_t)(w2 >> 32), (uint32_t)(w3 >> 32), (uint32_t)pos);
+    }
+}
+
+// k-mer table.  For rank i let f(i) be the smallest k-base string x with
+// S_SA[i] < x: the suffix's k-base prefix plus one when it has k bases or
+// more, else the suffix padded with A (a suffix that is a proper prefix of x
+// sorts before x).  f is non-decreasing along the suffix array, and
+// kmer[x] = #{i : f(i) <= x} = #{suffixes sorting before x}.  Thread i writes
+// kmer[x] = i for f(i-1) <= x < f(i), with f(-1) = 0 and f(n) = 4^k + 1, so
+// every entry is written once.
+__device__ __forceinline__ uint64_t kmer_f(const uint4 *rec, uint64_t i, uint64_t n, uint32_t k) {
+    const uint4 r0 = rec[2 * i];
+    const uint32_t pos = rec[2 * i + 1].w;
+    const uint64_t w0 = ((uint64_t)r0.y << 32) | r0.x;
+    const uint64_t x = w0 >> (64u - 2u * k);
+    return (n - pos) >= k ? x + 1 : x;
+}
+
+__global__ void build_kmer_kernel(const uint4 *__restrict__ rec, uint64_t n, uint32_t k, uint32_t *kmer) {
+    const uint64_t top = (1ull << (2 * k)) + 1;
+    GS_LOOP(i, n + 1) {
+        const uint64_t fa = i == 0 ? 0 : kmer_f(rec, i - 1, n, k);
+        const uint64_t fb = i == n ? top : kmer_f(rec, i, n, k);
+        for (uint64_t x = fa; x < fb; x++) kmer[x] = (uint32_t)i;
+    }
+}
+
+cudaError_t launch_build_kmer(sa_index *idx, cudaStream_t s) {
+    if (!idx->kmer) return cudaSuccess;
+    build_kmer_kernel<<<grid_for(idx->n + 1), kThreads, 0, s>>>(idx->rec, idx->n, idx->kmer_k, idx->kmer);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_records(sa_index *idx, cudaStream_t s) {
+    const unsigned g = grid_for(idx->n);
+    if (idx->width == 4)
+        build_records_kernel<uint32_t><<<g, kThreads, 0, s>>>(idx->text, reinterpret_cast<const uint32_t *>(idx->sa),
+                                                              idx->n, idx->rec);
+    else
+        build_records_kernel<uint64_t><<<g, kThreads, 0, s>>>(idx->text, reinterpret_cast<const uint64_t *>(idx->sa),
+                                                              idx->n, idx->rec);
+    return cudaGetLastError();
+}
+
 }  // namespace sa

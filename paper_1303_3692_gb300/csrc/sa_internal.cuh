@@ -8,9 +8,11 @@
 //   and every packed text carries SA_PAD_WORDS zero words after its last
 //   word, so a 32-base window starting at any base < n reads in bounds.
 //
-// Packed queries: query q starts at word ((q_offsets[q] - q_offsets[0]) >> 5) + q of the query
-// word buffer.  For consecutive queries this start grows by at least
-// ceil(m_q / 32) words, so no scan is needed to place them.
+// Packed queries: query q occupies 32-byte slots starting at slot
+// ((q_offsets[q] - q_offsets[0]) >> 7) + q of the query word buffer (4 words
+// per slot).  For consecutive queries the start grows by at least
+// ceil(m_q / 128) slots, so no scan is needed to place them, and a query's
+// first 128 bases sit in one aligned 32-byte sector.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -29,11 +31,13 @@ struct RefDesc {
     const void *sa;         // n entries of width 4 or 8
     const uint4 *keys;      // 2^depth key entries: 64 bases as two words (x,y = w0; z,w = w1)
     const uint8_t *keylen;  // 2^depth clamp lengths min(64, n - SA[rank])
+    const uint4 *rec;       // 2n uint4: n 32-byte suffix records, see sa_index::rec
+    const uint32_t *kmer;   // 4^kmer_k + 1 entries, see sa_index::kmer (null: none)
     uint64_t n;
     uint32_t depth;         // key-table depth d of this index; K = 2^d - 1 samples
     uint32_t smem_off;      // byte offset of this table in the search kernel's shared memory
     uint32_t use_depth;     // depth the search uses (<= depth); 0 = no table
-    uint32_t pad;
+    uint32_t kmer_k;        // k of the k-mer table (0: none)
 };
 
 // The compare outcome of the three cases of Section IV.
@@ -97,6 +101,14 @@ __device__ __forceinline__ uint32_t base_code(uint32_t c) {
     return ok ? code : 4u;
 }
 
+// First 32-byte slot of a query whose bases start at byte a_rel of the batch.
+__host__ __device__ __forceinline__ uint64_t query_slot(uint64_t a_rel, uint64_t q) { return (a_rel >> 7) + q; }
+
+// Per-query record written by the pack kernel for the search: x, y = the
+// starting bracket (L, R) of the binary search (L = 0xFFFFFFFF for -1), z = m
+// (kQueryInvalid for a query that cannot be searched), w = its first slot.
+constexpr uint32_t kQueryInvalid = 0xFFFFFFFFu;
+
 template <typename IdxT>
 __device__ __forceinline__ uint64_t sa_at(const void *sa, uint64_t i) {
     return (uint64_t)__ldg(reinterpret_cast<const IdxT *>(sa) + i);
@@ -117,6 +129,14 @@ struct sa_index {
     void *sa;            // device
     uint4 *keys;         // device, 2^depth entries
     uint8_t *keylen;     // device, 2^depth entries
+    uint4 *rec;          // device, n 32-byte records in suffix-array order (2 uint4 each):
+                         // the first 112 bases of suffix SA[i] as packed words w0, w1, w2
+                         // (bases 0-95) and the 16 bases 96-111 in the high-to-low bits of a
+                         // 32-bit word, then SA[i]: {w0.lo, w0.hi, w1.lo, w1.hi}, {w2.lo,
+                         // w2.hi, w3, SA[i]}
+    uint32_t *kmer;      // device, 4^kmer_k + 1 entries: kmer[x] = number of suffixes that
+                         // sort before the k-base string x (x as a 2k-bit number); null if none
+    uint32_t kmer_k;
     uint64_t device_bytes;
 };
 
@@ -131,13 +151,15 @@ int device_sm_count();
 // Kernels launched from the API translation unit.
 cudaError_t launch_pack_text(const char *ascii, uint64_t n, uint64_t *words, uint64_t nwords_padded,
                              int *err_flag, cudaStream_t s);
-cudaError_t launch_pack_queries(const char *ascii, const uint64_t *q_off, uint64_t first, uint64_t total,
-                                uint64_t n_q, uint64_t *qwords, int *err_flag, cudaStream_t s);
+struct SearchLaunch;
+cudaError_t launch_pack_queries(const SearchLaunch &L, int *err_flag, cudaStream_t s);
 int build_suffix_array(sa_index *idx, cudaStream_t s);
 cudaError_t launch_build_keys(sa_index *idx, cudaStream_t s);
+cudaError_t launch_build_records(sa_index *idx, cudaStream_t s);
+cudaError_t launch_build_kmer(sa_index *idx, cudaStream_t s);
 
 // Descriptors of every index a call uses, passed by value as a kernel
-// parameter (64 x 48 bytes, inside the 4 KB parameter space).
+// parameter (64 x 72 bytes; kernel parameters may take up to 32 KB).
 struct RefTable {
     RefDesc r[SA_MAX_REFS];
 };
@@ -147,12 +169,13 @@ struct SearchLaunch {
     uint32_t n_refs;
     uint32_t width;
     const char *ascii;        // query bases, indexed by q_off[q] - first
-    const uint64_t *qwords;   // packed queries
+    uint64_t *qwords;         // packed queries (written by the pack kernel)
     const uint64_t *q_off;    // n_q + 1 offsets
     uint64_t first;           // q_off[0]
     uint64_t total;           // q_off[n_q] - q_off[0]: query ranges past it are invalid
     const uint32_t *q_ref;    // null when n_refs == 1
     uint64_t n_q;
+    uint4 *meta;              // n_q per-query records from the pack kernel
     sa_result *out;
     const int *pack_err;      // device flag: a query had a non-ACGT byte
     unsigned long long *counter;

@@ -23,6 +23,8 @@
 // search_plain_kernel (comparison point).  Alg. 1 as printed, on a GPU: one
 //   thread per query, two full binary searches over [-1, n), bases compared
 //   one at a time.
+#include <type_traits>
+
 #include "sa_internal.cuh"
 
 namespace sa {
@@ -32,9 +34,12 @@ namespace {
 struct SmemDesc {
     const uint64_t *text;
     const void *sa;
+    const uint4 *rec;
+    const uint32_t *kmer;
     uint64_t n;
     uint32_t off;
     uint32_t depth;
+    uint32_t kmer_k;
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -171,20 +176,87 @@ __device__ __forceinline__ int cmp_suffix32(const uint64_t *__restrict__ T, uint
     }
 }
 
+// One window of a compare: q and t hold qlen and tlen bases (tlen may be 0)
+// aligned at the top bits, starting at base `off` of the query.  Returns 2
+// when the window does not decide, else the outcome with *lcp set.
+__device__ __forceinline__ int cmp_window(uint64_t q, uint64_t t, uint32_t qlen, uint32_t tlen, uint32_t off,
+                                          uint32_t m, uint32_t *lcp) {
+    const uint64_t x = q ^ t;
+    const uint32_t d = x ? ((uint32_t)__clzll((long long)x) >> 1) : 32u;
+    if (d < min(qlen, tlen)) {
+        *lcp = off + d;
+        return q < t ? CMP_LESS : CMP_GREATER;
+    }
+    if (tlen < qlen) {
+        *lcp = off + tlen;
+        return CMP_GREATER;
+    }
+    if (off + qlen >= m) {
+        *lcp = m;
+        return CMP_PREFIX;
+    }
+    return 2;
+}
+
+// P (first 64 bases q0, q1, then Q; length m) against a 32-byte suffix record
+// (r0 = bases 0-63, r1 = bases 64-95, 96-111 and the position).  Sets
+// *undecided when all 112 bases agree, m > 112 and the suffix has 112 bases
+// or more; the compare then continues in the text.
+__device__ __forceinline__ int cmp_record(uint64_t q0, uint64_t q1, const uint64_t *__restrict__ Q, uint32_t m,
+                                          uint4 r0, uint4 r1, uint32_t n, uint32_t *lcp, bool *undecided) {
+    const uint32_t klen = min(112u, n - r1.w);
+    int c = cmp_window(q0, ((uint64_t)r0.y << 32) | r0.x, min(32u, m), min(32u, klen), 0u, m, lcp);
+    if (c != 2) return c;
+    c = cmp_window(q1, ((uint64_t)r0.w << 32) | r0.z, min(32u, m - 32u), min(32u, klen - 32u), 32u, m, lcp);
+    if (c != 2) return c;
+    c = cmp_window(__ldg(Q + 2), ((uint64_t)r1.y << 32) | r1.x, min(32u, m - 64u), min(32u, klen - 64u), 64u, m,
+                   lcp);
+    if (c != 2) return c;
+    c = cmp_window(__ldg(Q + 3) & 0xFFFFFFFF00000000ull, (uint64_t)r1.z << 32, min(16u, m - 96u),
+                   min(16u, klen - 96u), 96u, m, lcp);
+    if (c != 2) return c;
+    *undecided = true;
+    *lcp = 112;
+    return CMP_PREFIX;
+}
+
 // The search of one query is a sequence of steps, one compare each, run by
 // its lane one step per loop iteration so that the 32 lanes of a warp stay in
 // the same short code path:
-//   init      read the query's offsets and first 64 bases;
+//   init      read the query's record from the pack kernel (length, slot and
+//             starting bracket) and its first 64 bases; when the index has a
+//             k-mer table and m >= k the bracket comes from the table entries
+//             of its first k bases and the descent is skipped;
 //   descent   compare with the key of level-order node k in shared memory
 //             (k = 0 once the table's depth is passed or the bounds split);
-//   deep      load SA[M] for M = L + (R - L)/2 and compare with the text.
+//   deep      load the suffix record of rank M = L + (R - L)/2 (32 bytes: 112
+//             bases and SA[M]) and compare; only when all 112 bases tie does
+//             the compare continue in the packed text.
 // Ranks are 32-bit modular: L = 0xFFFFFFFF stands for -1, and since every
 // rank is in [-1, n] with n < 2^32 - 1, R - L and L + (R - L)/2 are exact.
 // phase 0: both bounds share (L, R); a prefix match splits them into the
 // lower bound in (L, M] (phase 1) and the upper bound in [M, R), kept in
 // (HL, HR) until phase 1 ends (phase 2).
-template <typename IdxT, bool kSingle>
-__global__ void __launch_bounds__(1024, 1) search_kernel(const __grid_constant__ SearchLaunch a) {
+// Launch-bound variants: kOcc = 1 (1024 threads, <= 64 registers), 3 (512
+// threads x 3 CTAs, <= 40 registers), 8 (256 threads x 8 CTAs, <= 32 registers).
+template <int kOcc>
+struct Occ;
+template <>
+struct Occ<1> {
+    static constexpr int threads = 1024, blocks = 1;
+};
+template <>
+struct Occ<3> {
+    static constexpr int threads = 512, blocks = 3;
+};
+template <>
+struct Occ<8> {
+    static constexpr int threads = 256, blocks = 8;
+};
+
+template <typename IdxT, bool kSingle, int kOcc>
+__global__ void __launch_bounds__(Occ<kOcc>::threads, Occ<kOcc>::blocks)
+    search_kernel(const __grid_constant__ SearchLaunch a) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ SmemDesc sdesc[SA_MAX_REFS];
     __shared__ __align__(8) uint64_t mbar;
@@ -192,7 +264,7 @@ __global__ void __launch_bounds__(1024, 1) search_kernel(const __grid_constant__
 
     for (unsigned r = tid; r < a.n_refs; r += blockDim.x) {
         const RefDesc &d = a.refs.r[r];
-        sdesc[r] = SmemDesc{d.text, d.sa, d.n, d.smem_off, d.use_depth};
+        sdesc[r] = SmemDesc{d.text, d.sa, d.rec, d.kmer, d.n, d.smem_off, d.use_depth, d.kmer_k};
     }
     if (tid == 0) {
         mbar_init(&mbar, 1);
@@ -228,6 +300,9 @@ __global__ void __launch_bounds__(1024, 1) search_kernel(const __grid_constant__
     const SmemDesc d0 = sdesc[0];
     const uint64_t *T = d0.text;
     const void *SAp = d0.sa;
+    const uint4 *REC = d0.rec;
+    const uint32_t *KM = d0.kmer;
+    uint32_t kk = d0.kmer_k;
     uint32_t n = (uint32_t)d0.n;
     const uint8_t *Ktab = smem + d0.off;
     uint32_t depth = d0.depth;
@@ -271,10 +346,9 @@ __global__ void __launch_bounds__(1024, 1) search_kernel(const __grid_constant__
 
         if (fresh) {
             fresh = false;
-            const uint64_t a0 = __ldg(a.q_off + q) - a.first;
-            const uint64_t a1 = __ldg(a.q_off + q + 1) - a.first;
+            const uint4 mt = __ldg(a.meta + q);
             const uint32_t r = (!kSingle && a.q_ref) ? __ldg(a.q_ref + q) : 0u;
-            if (bad_batch || r >= a.n_refs || a1 < a0 || a1 > a.total || a1 - a0 >= (1ull << 31)) {
+            if (bad_batch || mt.z == kQueryInvalid || r >= a.n_refs) {
                 write_result(a.out, q, ~0ull, ~0ull);
                 active = false;
                 continue;
@@ -283,24 +357,37 @@ __global__ void __launch_bounds__(1024, 1) search_kernel(const __grid_constant__
                 const SmemDesc d = sdesc[r];
                 T = d.text;
                 SAp = d.sa;
+                REC = d.rec;
+                KM = d.kmer;
+                kk = d.kmer_k;
                 n = (uint32_t)d.n;
                 Ktab = smem + d.off;
                 depth = d.depth;
             }
-            m = (uint32_t)(a1 - a0);
+            m = mt.z;
             if (m == 0) {
                 write_result(a.out, q, 0, n);
                 active = false;
                 continue;
             }
-            Q = a.qwords + (a0 >> 5) + q;
-            q0 = __ldg(Q);
-            q1 = m > 32 ? __ldg(Q + 1) : 0ull;
-            L = 0xFFFFFFFFu;
-            R = n;
+            Q = a.qwords + 4 * (size_t)mt.w;
+            const ulonglong2 qw = __ldg(reinterpret_cast<const ulonglong2 *>(Q));
+            q0 = qw.x;
+            q1 = qw.y;
             lcpL = lcpR = 0;
             phase = 0;
-            k = depth ? 1u : 0u;
+            L = mt.x;  // the pack kernel's bracket: the k-mer table's, or [-1, n)
+            R = mt.y;
+            if (KM != nullptr && m >= kk) {
+                k = 0;
+                if (R - L <= 1u) {
+                    write_result(a.out, q, R, R);
+                    active = false;
+                    continue;
+                }
+            } else {
+                k = depth ? 1u : 0u;
+            }
         }
 
         int c;
@@ -319,8 +406,11 @@ __global__ void __launch_bounds__(1024, 1) search_kernel(const __grid_constant__
             k = (c == CMP_PREFIX || nk >= (1u << depth)) ? 0u : nk;
         } else {
             M = L + ((R - L) >> 1);
-            const uint32_t p = (uint32_t)sa_at<IdxT>(SAp, M);
-            c = cmp_suffix32(T, n, p, Q, m, min(lcpL, lcpR), &l);
+            const uint4 r0 = __ldg(REC + 2 * (size_t)M);
+            const uint4 r1 = __ldg(REC + 2 * (size_t)M + 1);
+            bool und = false;
+            c = cmp_record(q0, q1, Q, m, r0, r1, n, &l, &und);
+            if (und) c = cmp_suffix32(T, n, r1.w, Q, m, max(112u, min(lcpL, lcpR)), &l);
         }
         if (c == CMP_PREFIX && phase == 0) {
             HL = M;
@@ -384,7 +474,7 @@ __global__ void __launch_bounds__(256) search_plain_kernel(const __grid_constant
         return;
     }
     const uint32_t m = (uint32_t)(a1 - a0);
-    const uint64_t *Q = a.qwords + (a0 >> 5) + q;
+    const uint64_t *Q = a.qwords + 4 * query_slot(a0, q);
     const RefDesc &d = a.refs.r[r];
     const uint64_t *T = d.text;
     const uint64_t n = d.n;
@@ -418,14 +508,26 @@ cudaError_t launch_search(const SearchLaunch &L, cudaStream_t s) {
     if (L.n_q == 0) return cudaSuccess;
     const size_t smem = L.smem_bytes;
     const bool single = L.n_refs == 1 && L.q_ref == nullptr;
+    const uint32_t resident = L.threads * (L.blocks / (uint32_t)device_sm_count());
     auto go = [&](auto kernel) {
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kernel<<<L.blocks, L.threads, smem, s>>>(L);
     };
+    // The register cap follows the threads resident per SM.
+    auto pick = [&](auto idx_tag, auto single_tag) {
+        using I = decltype(idx_tag);
+        constexpr bool S = decltype(single_tag)::value;
+        if (L.threads <= 256 && resident > 1536)
+            go(search_kernel<I, S, 8>);
+        else if (L.threads <= 512 && resident > 1024)
+            go(search_kernel<I, S, 3>);
+        else
+            go(search_kernel<I, S, 1>);
+    };
     if (L.width == 4)
-        single ? go(search_kernel<uint32_t, true>) : go(search_kernel<uint32_t, false>);
+        single ? pick(uint32_t{}, std::true_type{}) : pick(uint32_t{}, std::false_type{});
     else
-        single ? go(search_kernel<uint64_t, true>) : go(search_kernel<uint64_t, false>);
+        single ? pick(uint64_t{}, std::true_type{}) : pick(uint64_t{}, std::false_type{});
     return cudaGetLastError();
 }
 

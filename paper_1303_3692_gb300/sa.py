@@ -33,6 +33,8 @@ SA_ERR_IO = -7
 SA_ERR_FORMAT = -8
 SA_W32 = 0x1
 SA_W64 = 0x2
+SA_NO_KMER = 0x4
+SA_PARAM_Q_RANGE = 0x1
 SA_LOCATE_NOALLOC_MAX_QUERIES = 1 << 26
 
 _u64 = ctypes.c_uint64
@@ -52,7 +54,8 @@ class sa_result(ctypes.Structure):
 
 class sa_search_params(ctypes.Structure):
     _fields_ = [("threads_per_block", _u32), ("blocks_per_sm", _u32), ("key_depth", _u32), ("chunk", _u32),
-                ("search_events", _vp * 2), ("reserved", _u32 * 4)]
+                ("search_events", _vp * 2), ("flags", _u32), ("reserved0", _u32), ("q_first", _u64),
+                ("q_total", _u64), ("reserved", _u32 * 4)]
 
 
 # Every symbol include/sa.h declares, with its ctypes signature.
@@ -67,7 +70,8 @@ SIGNATURES = {
     "sa_save": (ctypes.c_int, [_vp, ctypes.c_char_p, _vp]),
     "sa_load": (ctypes.c_int, [ctypes.c_char_p, _vp, ctypes.POINTER(_vp)]),
     "sa_index_info": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u32), ctypes.POINTER(_u32),
-                                     ctypes.POINTER(_u64)]),
+                                     ctypes.POINTER(_u32), ctypes.POINTER(_u64)]),
+    "sa_copy_kmer_table": (ctypes.c_int, [_vp, _vp, _vp]),
     "sa_copy_suffix_array": (ctypes.c_int, [_vp, _vp, _vp]),
     "sa_free": (None, [_vp]),
     "sa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -133,10 +137,10 @@ class Index:
 
     def __init__(self, handle: int):
         self._h = _vp(handle)
-        n, w, d, b = _u64(), _u32(), _u32(), _u64()
-        _check(lib().sa_index_info(self._h, ctypes.byref(n), ctypes.byref(w), ctypes.byref(d), ctypes.byref(b)),
-               "sa_index_info")
-        self.n, self.width, self.key_depth, self.device_bytes = n.value, w.value, d.value, b.value
+        n, w, d, k, b = _u64(), _u32(), _u32(), _u32(), _u64()
+        _check(lib().sa_index_info(self._h, ctypes.byref(n), ctypes.byref(w), ctypes.byref(d), ctypes.byref(k),
+                                   ctypes.byref(b)), "sa_index_info")
+        self.n, self.width, self.key_depth, self.kmer_k, self.device_bytes = n.value, w.value, d.value, k.value, b.value
 
     @property
     def handle(self):
@@ -164,15 +168,32 @@ class Index:
             torch.cuda.current_stream().synchronize()
         return out
 
+    def kmer_table(self, device="cuda"):
+        """The k-mer table (4^k + 1 counts) as an int64 tensor (a copy)."""
+        if not self.kmer_k:
+            raise ValueError("index has no k-mer table")
+        out = torch.empty((1 << (2 * self.kmer_k)) + 1, dtype=torch.int32, device=device)
+        _check(lib().sa_copy_kmer_table(self.handle, _ptr(out), _stream(None)), "sa_copy_kmer_table")
+        if out.is_cuda:
+            torch.cuda.current_stream().synchronize()
+        return out.to(torch.int64) & 0xFFFFFFFF
+
     def save(self, path: str):
         sa_save(self, path)
 
 
-def sa_build(text, width: int = 32, stream=None) -> Index:
-    """Index one reference (ASCII bases, host or device)."""
+def sa_build(text, width: int = 32, stream=None, kmer_k: Optional[int] = None) -> Index:
+    """Index one reference (ASCII bases, host or device).  kmer_k: None picks k
+    automatically, 0 builds no k-mer table, 1..15 sets k."""
     flags = SA_W32 if width == 32 else SA_W64 if width == 64 else None
     if flags is None:
         raise ValueError("width must be 32 or 64")
+    if kmer_k == 0:
+        flags |= SA_NO_KMER
+    elif kmer_k is not None:
+        if not 1 <= kmer_k <= 15:
+            raise ValueError("kmer_k must be 0..15")
+        flags |= kmer_k << 8
     n = int(text.numel() if torch is not None and isinstance(text, torch.Tensor) else len(text))
     h = _vp()
     _check(lib().sa_build(_ptr(text), n, flags, _stream(stream), ctypes.byref(h)), "sa_build")
@@ -194,7 +215,8 @@ def sa_free(idx: Index):
 
 
 def sa_index_info(idx: Index):
-    return {"n": idx.n, "width": idx.width, "key_depth": idx.key_depth, "device_bytes": idx.device_bytes}
+    return {"n": idx.n, "width": idx.width, "key_depth": idx.key_depth, "kmer_k": idx.kmer_k,
+            "device_bytes": idx.device_bytes}
 
 
 def _refs(refs) -> tuple:

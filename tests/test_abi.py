@@ -58,11 +58,12 @@ def test_host_side_argument_checks(salib):
     assert L.sa_build(ctypes.cast(buf, ctypes.c_void_p), 4, 3, None, ctypes.byref(h)) == salib.SA_ERR_ARG
     assert L.sa_search_batch(None, 1, None, None, None, 1, None, None) == salib.SA_ERR_ARG
     assert L.sa_locate(None, 1, None, None, 1, 4, None, None, 0, None) == salib.SA_ERR_ARG
-    assert L.sa_index_info(None, None, None, None, None) == salib.SA_ERR_ARG
+    assert L.sa_index_info(None, None, None, None, None, None) == salib.SA_ERR_ARG
+    assert L.sa_copy_kmer_table(None, None, None) == salib.SA_ERR_ARG
     assert L.sa_save(None, b"/nonexistent", None) == salib.SA_ERR_ARG
     L.sa_free(None)
 
 
 def test_result_struct_layout(salib):
     assert ctypes.sizeof(salib.sa_result) == 24
-    assert ctypes.sizeof(salib.sa_search_params) == 48
+    assert ctypes.sizeof(salib.sa_search_params) == 72

@@ -170,7 +170,9 @@ def test_host_buffers_match_device_buffers(sa):
 
 @pytest.mark.parametrize("params", [dict(key_depth=1), dict(key_depth=5), dict(key_depth=13),
                                     dict(threads_per_block=128, blocks_per_sm=4, chunk=32),
-                                    dict(threads_per_block=512, blocks_per_sm=2, chunk=256)])
+                                    dict(threads_per_block=512, blocks_per_sm=2, chunk=256),
+                                    dict(threads_per_block=512, blocks_per_sm=3, key_depth=12),
+                                    dict(threads_per_block=256, blocks_per_sm=8, key_depth=10, chunk=16)])
 def test_tuning_knobs_do_not_change_results(sa, params):
     ref = datagen.reference(200_000, 31, sd_cover=0.1, tandem_cover=0.02)
     T = oracle.normalize(ref)
@@ -270,3 +272,50 @@ def test_plain_small_config_full_size(sa):
     assert (hi - lo)[w.sampled].min() >= 1
     for q in np.nonzero(w.sampled)[0][:100]:
         assert oracle.bruteforce(T, w.q_bases[w.q_offsets[q]:w.q_offsets[q + 1]])[0] == hi[q] - lo[q]
+
+
+@pytest.mark.parametrize("n,k", [(11, 1), (11, 2), (700, 3), (700, 5), (20000, 6), (20000, 0)])
+def test_kmer_table_and_search_by_k(sa, n, k):
+    ref = datagen.reference(n, 50 + n, tandem_cover=0.1) if n > 11 else np.frombuffer(b"ACGGTACGTAC", np.uint8)
+    T = oracle.normalize(ref)
+    osa = oracle.sa_naive(T)
+    idx = sa.sa_build(_dev(ref), kmer_k=k)
+    assert idx.kmer_k == k
+    if k:
+        assert np.array_equal(idx.kmer_table().cpu().numpy(), oracle.kmer_table(T, osa, k))
+    qb, qo, _ = datagen.queries(ref, 2000, 51, m=(1, 130), frac_sampled=0.6, subs=(0, 1))
+    _check_search(sa, idx, T, osa, qb, qo, plain=False)
+
+
+def test_kmer_table_full_default_k(sa):
+    ref = datagen.reference(300_000, 61, sd_cover=0.1, tandem_cover=0.02)
+    T = oracle.normalize(ref)
+    idx = sa.sa_build(_dev(ref))
+    osa = idx.suffix_array().cpu().numpy().astype(np.int64)
+    assert oracle.verify_sa(T, osa, threads=oracle.cpu_threads())[0] == 0
+    assert idx.kmer_k == 10  # largest k with 4^k <= 4n
+    assert np.array_equal(idx.kmer_table().cpu().numpy(), oracle.kmer_table(T, osa, idx.kmer_k))
+
+
+def test_q_range_param_sub_batch(sa):
+    """A sub-batch whose offsets start inside a larger buffer, with and without
+    the caller-stated range (no host read-back); a range that is too small
+    marks the batch invalid instead of reading past it."""
+    ref = datagen.reference(50_000, 71, sd_cover=0.1)
+    T = oracle.normalize(ref)
+    idx = sa.sa_build(_dev(ref))
+    osa = oracle.sa_naive(T)
+    qb, qo, _ = datagen.queries(ref, 1000, 72, m=(10, 140), frac_sampled=0.7, subs=(0, 1))
+    sub = qo[100:601]
+    qb_d, sub_d = _dev(qb), _dev(sub)
+    p = sa.sa_search_params()
+    p.flags = sa.SA_PARAM_Q_RANGE
+    p.q_first, p.q_total = int(sub[0]), int(sub[-1] - sub[0])
+    a = sa.sa_search_batch(idx, qb_d, sub_d, params=p).cpu()
+    b = sa.sa_search_batch(idx, qb_d, sub_d).cpu()
+    assert torch.equal(a, b)
+    lo, hi = oracle.search_batch(T, osa, qb[sub[0]:sub[-1]], sub - sub[0])
+    assert np.array_equal(a[:, 0].numpy(), lo) and np.array_equal(a[:, 1].numpy(), hi)
+    p.q_total = int(sub[-1] - sub[0]) - 5
+    c = sa.sa_search_batch(idx, qb_d, sub_d, params=p).cpu()
+    assert (c == -1).all()

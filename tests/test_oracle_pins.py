@@ -216,3 +216,42 @@ def test_probe_model_closed_forms():
     P = T[1000:1012]
     pr, ch, lo, hi = oracle.probe_model(T, sa, P, d0=0)
     assert (lo, hi) == oracle.search(T, sa, P) and hi > lo
+
+
+def _brute_kmer_table(text: str, k: int):
+    sufs = [text[i:] for i in range(len(text))]
+    out = []
+    for x in range(4 ** k):
+        s = "".join("ACGT"[(x >> (2 * (k - 1 - t))) & 3] for t in range(k))
+        out.append(sum(1 for u in sufs if u < s))  # Python's order: a proper prefix sorts first
+    return out + [len(text)]
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_kmer_table_against_brute_force(k):
+    """table[x] = #suffixes sorting before the k-string x, including short
+    suffixes that fall between two k-strings (e.g. AG between ACT and AGA)."""
+    rng = np.random.default_rng(k)
+    texts = ["ACGTAG", "AG", "A", "TTTT", "ACTAGAAG"] + ["".join(rng.choice(list("ACGT"), L)) for L in (5, 9, 17, 40)]
+    for text in texts:
+        T = oracle.normalize(text)
+        sa = oracle.sa_naive(T)
+        assert oracle.kmer_table(T, sa, k).tolist() == _brute_kmer_table(text, k), text
+
+
+def test_kmer_model_matches_search():
+    ref = datagen.reference(6000, 14, tandem_cover=0.1, sd_cover=0.0)
+    T = oracle.normalize(ref)
+    sa = oracle.sa_naive(T)
+    for k in (3, 5):
+        tab = oracle.kmer_table(T, sa, k)
+        qb, qo, _ = datagen.queries(ref, 300, 15, m=(1, 120), frac_sampled=0.6, subs=(0, 1))
+        for q in range(300):
+            P = qb[qo[q]:qo[q + 1]]
+            pr, wi, tr, lo, hi = oracle.probe_model_kmer(T, sa, tab, k, P, d0=0)
+            assert (lo, hi) == oracle.search(T, sa, P)
+            if P.size >= k:
+                x = int("".join("0123"["ACGT".index(chr(c))] for c in P[:k]), 4)
+                s = tab[x + 1] - tab[x]
+                assert tr == 1 and pr <= 2 * int(np.ceil(np.log2(s + 2)))
+                assert tab[x] - 1 <= lo <= hi <= tab[x + 1]
