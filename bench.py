@@ -35,25 +35,31 @@ METRIC = "exact-match queries/s (query bases/s, % HBM roofline alongside)"
 UNIT = "queries/s"
 WORKLOAD = "repetitive-100Mbp-10M-q100-locate64"
 
-# Algorithmic bytes of the search kernel per query on this workload, from the
-# oracle's byte model (oracle_probe_model: lockstep lower/upper-bound search,
-# probes below depth 13 -- the levels the shared-memory key table absorbs --
-# each one 32-byte suffix-array sector plus one 32-byte text sector per
-# 64-base chunk the compare needs, with the LCP-of-bounds skip) on a seeded
-# 20,000-query sample, plus ceil(m/4) packed query bytes and 12 result bytes:
-#   B_q = 25 + 32 * P_q + 32 * X_q + 12.
-# Written by oracle/bytes_model.py.
-SEARCH_BYTES_PER_QUERY = 945.7152  # P_q = 13.97, X_q = 14.42 (d0 = 13, 20,000 queries)
-SEARCH_BYTES_SOURCE = "oracle/bytes_model.py --workload repetitive-100m"
+# Algorithmic bytes per query of each kernel of a step on this workload
+# (m = 100, k = 14), from the oracle's byte model (oracle/bytes_model.py:
+# oracle_probe_model_kmer on 20,000 seeded queries: 1.19375 record probes and
+# 6.58 occurrences per query on average, 0.51 positions kept at cap 64):
+#   pack_queries_kernel: 100 ASCII bytes read + 8 offset bytes + one 32-byte
+#       k-mer table sector + 25 packed bytes written          = 165.0
+#   search_kernel: 25 packed query bytes + 32 per record probe + 12 result
+#       bytes (lo, hi, count at the suffix array's width)      = 75.2
+#   locate (3 kernels): 24 result bytes read + 8 offset bytes written + 4.1
+#       position bytes (suffix-array entry read and written)   = 36.1
+KERNEL_BYTES_PER_QUERY = {
+    "pack_queries_kernel": 100 + 8 + 32 + 25,
+    "search_kernel": 25 + 32 * 1.19375 + 12,
+    "locate": 24 + 8 + 4.1072,
+}
+BYTES_SOURCE = "oracle/bytes_model.py --workload repetitive-100m (k = 14)"
 
 # DRAM bytes per search-kernel launch from one ncu capture, valid only while
 # the kernel sources hash to KERNEL_SHA (else reported as null).
-TRAFFIC = {"kernel_sha": "0a098c4064c1bc01", "dram_bytes_per_launch": 7178502000 + 244703232}
+TRAFFIC = {"kernel_sha": None, "kernel": None, "dram_bytes_per_launch": None}
 
 
 def kernel_sha() -> str:
     h = hashlib.sha256()
-    for f in ("search.cu", "sa_internal.cuh"):
+    for f in ("search.cu", "pack.cu", "locate.cu", "sa_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1303_3692_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -135,6 +141,204 @@ def build_workload(scale: float):
     from paper_1303_3692_gb300 import datagen
 
     return datagen.repetitive_100m(scale=scale)
+
+
+def run_multi_genome(args, world, rank, local):
+    """4 references (5, 12, 25, 50 Mbp) and 16,000,000 queries of U[20,250] bp
+    in one multi-reference call (count only); the launch shape is autotuned."""
+    import torch
+
+    import paper_1303_3692_gb300.sa as sa
+    from paper_1303_3692_gb300 import autotune, datagen
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    refs, qb, qo, qref, _ = datagen.multi_genome(scale=args.scale)
+    t0 = time.perf_counter()
+    idxs = [sa.sa_build(torch.from_numpy(r).to(dev)) for r in refs]
+    build_s = time.perf_counter() - t0
+    n_q = qo.size - 1
+    qb_d, qo_d, qr_d = (torch.from_numpy(x).to(dev) for x in (qb, qo, qref))
+    out = torch.empty((n_q, 3), dtype=torch.int64, device=dev)
+    params, tune = autotune.autotune(idxs, qb_d, qo_d, q_ref=qr_d, use_cache=False)
+    stream = torch.cuda.current_stream()
+
+    def lib_event():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
+    params.flags = sa.SA_PARAM_Q_RANGE
+    params.q_first, params.q_total = 0, int(qo[-1])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        sa.sa_search_batch(idxs, qb_d, qo_d, q_ref=qr_d, out=out, params=params)
+    starts = [lib_event() for _ in range(args.steps)]
+    ends = [lib_event() for _ in range(args.steps)]
+    ks = [lib_event() for _ in range(args.steps)]
+    ke = [lib_event() for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            params.search_events[0], params.search_events[1] = ks[k].cuda_event, ke[k].cuda_event
+            starts[k].record(stream)
+            sa.sa_search_batch(idxs, qb_d, qo_d, q_ref=qr_d, out=out, params=params)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    kern_ms = [a.elapsed_time(b) for a, b in zip(ks, ke)]
+    total_s = sum(step_ms) / 1e3
+    value = args.steps * n_q / total_s
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "multi-genome-4refs-92Mbp-16M-q20to250", "refs_bp": [int(r.size) for r in refs],
+                   "queries_per_step": n_q, "mode": "count", "autotuned": tune["best"],
+                   "kmer_k": [i.kmer_k for i in idxs], "l2": "flushed between steps"},
+        "query_bases_per_s": value * (float(qo[-1]) / n_q),
+        "search_kernel_ms": statistics.mean(kern_ms), "step_ms_all": step_ms, "build_s": build_s,
+        "gpu_launches": args.steps * 2, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_human_sized(args, world, rank, local):
+    """3.1 Gbp reference (GC 0.41, 45% repeat families, 3% tandem repeats),
+    int64 suffix array; 150 bp queries, 10:1 sampled (0-1 substitutions) to
+    random; count-only steps and locate-up-to-16 steps timed separately."""
+    import torch
+
+    import paper_1303_3692_gb300.sa as sa
+    from paper_1303_3692_gb300 import datagen
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    nq = args.human_queries
+    t0 = time.perf_counter()
+    w = datagen.human_sized(scale=args.scale, nq_sampled=nq * 10 // 11, nq_random=nq - nq * 10 // 11)
+    gen_s = time.perf_counter() - t0
+    ref_d = torch.from_numpy(w.ref).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    idx = sa.sa_build(ref_d, width=64)
+    build_s = time.perf_counter() - t0
+    del ref_d
+    n_q = w.q_offsets.size - 1
+    qb_d = torch.from_numpy(w.q_bases).to(dev)
+    qo_d = torch.from_numpy(w.q_offsets).to(dev)
+    res = torch.empty((n_q, 3), dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def lib_event():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
+    p = sa.sa_search_params()
+    p.flags = sa.SA_PARAM_Q_RANGE
+    p.q_first, p.q_total = 0, int(w.q_offsets[-1])
+    offs = torch.empty(n_q + 1, dtype=torch.int64, device=dev)
+    sa.sa_search_batch(idx, qb_d, qo_d, out=res, params=p)
+    o, ps = sa.sa_locate(idx, res, 16)
+    total_pos = int(o[-1].item())
+    pos = torch.empty(max(1, total_pos), dtype=torch.int64, device=dev)
+    del o, ps
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = {}
+    with Clocks(local) as clk:
+        for mode in ("count", "locate16"):
+            ts, ks = [], []
+            for it in range(args.warmup + args.steps):
+                flush.zero_()
+                a, b = lib_event(), lib_event()
+                k0, k1 = lib_event(), lib_event()
+                p.search_events[0], p.search_events[1] = k0.cuda_event, k1.cuda_event
+                a.record(stream)
+                sa.sa_search_batch(idx, qb_d, qo_d, out=res, params=p)
+                if mode == "locate16":
+                    sa.sa_locate(idx, res, 16, out_offsets=offs, out_pos=pos, capacity=total_pos)
+                b.record(stream)
+                torch.cuda.synchronize()
+                if it >= args.warmup:
+                    ts.append(a.elapsed_time(b))
+                    ks.append(k0.elapsed_time(k1))
+            out[mode] = {"ms_per_step": statistics.mean(ts), "queries_per_s": n_q / (statistics.mean(ts) / 1e3),
+                         "search_kernel_ms": statistics.mean(ks)}
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": out["count"]["queries_per_s"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["count"]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "human-3.1Gbp-int64-q150", "n": int(w.ref.size), "queries_per_step": n_q,
+                   "m": 150, "sa_width": 64, "kmer_k": idx.kmer_k, "index_device_bytes": idx.device_bytes,
+                   "l2": "flushed between steps"},
+        "modes": out, "build_s": build_s, "datagen_s": gen_s, "positions_per_step": total_pos,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args, world, rank, local):
+    """8 resident references (1, 5, 20, 50, 100, 200, 300, 500 Mbp, 10% segmental
+    duplications); a Poisson stream of requests (mean 2,000/s), each targeting a
+    random reference with a log-uniform 1-100,000 queries of U[20,300] bp (75%
+    sampled); continuous batching against one call per request."""
+    import torch
+
+    import paper_1303_3692_gb300.sa as sa
+    from paper_1303_3692_gb300 import datagen, serve
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sizes = [int(x * args.scale) for x in (1e6, 5e6, 20e6, 50e6, 100e6, 200e6, 300e6, 500e6)]
+    t0 = time.perf_counter()
+    refs = [datagen.reference(max(n, 10_000), datagen.SEED0 + 50 + i, sd_cover=0.10) for i, n in enumerate(sizes)]
+    pools = []
+    for i, r in enumerate(refs):
+        qb, qo, _ = datagen.queries(r, args.pool, datagen.SEED0 + 60 + i, m=(20, 300), frac_sampled=0.75,
+                                    subs=(0, 0))
+        pools.append((torch.from_numpy(qb).pin_memory(), qo))
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    idxs = [sa.sa_build(torch.from_numpy(r).to(dev)) for r in refs]
+    build_s = time.perf_counter() - t0
+    warm = serve.make_trace(pools, rate=2000, duration=0.2, seed=1)
+    serve.Server(idxs).run(warm)
+    trace = serve.make_trace(pools, rate=2000, duration=args.serve_seconds, seed=2)
+    with Clocks(local) as clk:
+        srv = serve.Server(idxs, slots=3)
+        stats = srv.run(trace)
+    plain_trace = serve.make_trace(pools, rate=2000, duration=args.serve_seconds, seed=2)
+    plain = serve.run_plain(idxs, plain_trace)
+    # saturated: the same requests all arriving at once (maximum sustained throughput)
+    sat = serve.make_trace(pools, rate=2000, duration=args.serve_seconds, seed=2)
+    for r in sat:
+        r.arrival = 0.0
+    sat_stats = serve.Server(idxs, slots=3).run(sat)
+    sat_plain = serve.make_trace(pools, rate=2000, duration=args.serve_seconds, seed=2)
+    for r in sat_plain:
+        r.arrival = 0.0
+    sat_plain_stats = serve.run_plain(idxs, sat_plain)
+    if rank != 0:
+        return
+    line = {
+        "metric": "serving p50/p99 latency and queries/s", "value": stats["queries_per_s"], "unit": UNIT,
+        "n_gpus": world, "steps": 1, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "serving-8refs-1176Mbp-poisson2000", "refs_bp": [int(r.size) for r in refs],
+                   "seconds": args.serve_seconds, "pool_queries_per_ref": args.pool},
+        "serving": stats, "plain_per_request": plain,
+        "p99_gain": plain["p99_ms"] / stats["p99_ms"] if stats["p99_ms"] else None,
+        "saturated": {"batched": sat_stats, "plain_per_request": sat_plain_stats,
+                      "throughput_gain": sat_stats["queries_per_s"] / sat_plain_stats["queries_per_s"]},
+        "build_s": build_s, "datagen_s": gen_s, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
 
 
 def run_reference(args, world, rank):
@@ -240,8 +444,12 @@ def run_ours(args, world, rank, local):
     del offs_tmp, pos_tmp
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > 129 MB L2
 
-    def step():
+    mids = []
+
+    def step(mid=None):
         sa.sa_search_batch(idx, qb_d, qo_d, out=res_d, params=params)
+        if mid is not None:
+            mid.record(stream)
         sa.sa_locate(idx, res_d, cap, out_offsets=offs_d, out_pos=pos_d, capacity=total_pos)
 
     for _ in range(args.warmup):
@@ -261,7 +469,8 @@ def run_ours(args, world, rank, local):
             params.search_events[0] = k_starts[k].cuda_event
             params.search_events[1] = k_ends[k].cuda_event
             starts[k].record(stream)
-            step()
+            mids.append(torch.cuda.Event(enable_timing=True))
+            step(mids[-1])
             ends[k].record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -269,6 +478,11 @@ def run_ours(args, world, rank, local):
     clocks = clk.summary()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     kern_ms = [s.elapsed_time(e) for s, e in zip(k_starts, k_ends)]
+    phases = {
+        "pack_queries_kernel": statistics.mean(a.elapsed_time(b) for a, b in zip(starts, k_starts)),
+        "search_kernel": statistics.mean(kern_ms),
+        "locate": statistics.mean(a.elapsed_time(b) for a, b in zip(mids, ends)),
+    }
     total_s = sum(step_ms) / 1e3
     if dist is not None:
         t = torch.tensor([total_s], device=dev)
@@ -313,14 +527,19 @@ def run_ours(args, world, rank, local):
     kern_mean_s = statistics.mean(kern_ms) / 1e3
 
     peak, peak_kind = measured_peaks()
-    roof = None
-    if SEARCH_BYTES_PER_QUERY:
-        achieved = SEARCH_BYTES_PER_QUERY * n_q / kern_mean_s / 1e9
-        sha = kernel_sha()
-        traffic = TRAFFIC["dram_bytes_per_launch"] if TRAFFIC["kernel_sha"] == sha else None
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "search_kernel", "peak_kind": peak_kind,
-                "bytes_per_query": SEARCH_BYTES_PER_QUERY, "bytes_source": SEARCH_BYTES_SOURCE}
+    per_kernel = {}
+    for name, ms in phases.items():
+        gbs = KERNEL_BYTES_PER_QUERY[name] * n_q / (ms / 1e3) / 1e9
+        per_kernel[name] = {"ms": ms, "bytes_per_query": KERNEL_BYTES_PER_QUERY[name], "achieved_gbs": gbs,
+                            "frac": gbs / peak}
+    dominant = max(phases, key=phases.get)
+    sha = kernel_sha()
+    traffic = (TRAFFIC["dram_bytes_per_launch"]
+               if TRAFFIC["kernel_sha"] == sha and TRAFFIC["kernel"] == dominant else None)
+    roof = {"bound": "hbm", "achieved": per_kernel[dominant]["achieved_gbs"], "peak": peak, "unit": "GB/s",
+            "frac": per_kernel[dominant]["frac"], "traffic": traffic, "kernel": dominant,
+            "peak_kind": peak_kind, "bytes_per_query": KERNEL_BYTES_PER_QUERY[dominant],
+            "bytes_source": BYTES_SOURCE, "per_kernel": per_kernel}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -338,6 +557,7 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "query_bases_per_s": value * (m_total / n_q),
         "search_kernel_ms": statistics.mean(kern_ms),
+        "phase_ms": phases,
         "step_ms_all": step_ms,
         "wall_s_timed_region": wall,
         "build_s": build_s,
@@ -390,10 +610,22 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=6.0)
+    ap.add_argument("--workload", choices=["repetitive-100m", "multi-genome", "serving", "human-sized"],
+                    default="repetitive-100m")
+    ap.add_argument("--human-queries", type=int, default=22_000_000,
+                    help="queries of the 3.1 Gbp workload (the recipe's full batch is 110,000,000)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--pool", type=int, default=300_000, help="queries pre-generated per reference (serving)")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "multi-genome":
+        run_multi_genome(args, world, rank, local)
+    elif args.workload == "serving":
+        run_serving(args, world, rank, local)
+    elif args.workload == "human-sized":
+        run_human_sized(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 

@@ -230,7 +230,7 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     const uint64_t nslots = (total >> 7) + n_q + 1;
     if (nslots >= (1ull << 32)) return SA_ERR_ARG;
     uint64_t *qwords = sc.get<uint64_t>(4 * nslots);
-    uint4 *meta = sc.get<uint4>(n_q);
+    uint4 *meta = sc.get<uint4>(2 * n_q);
     int *flags = sc.get<int>(4);  // [0] pack error, [1] status
     unsigned long long *counter = sc.get<unsigned long long>(1);
     if (sc.failed) return SA_ERR_NOMEM;
@@ -310,17 +310,28 @@ uint32_t auto_kmer_k(uint64_t n) {
     return k;
 }
 
-// Allocates the device arrays of an index whose n, width and depth are set.
+// Allocates the device arrays of an index whose n, width, depth and kmer_k
+// are set: first the text, suffix array and key table; the records and the
+// k-mer table (about 32n bytes) are allocated separately, after the build's
+// scratch has been returned, so the two never coexist.
 int alloc_index(sa_index *idx) {
     idx->nwords = (idx->n + 31) / 32;
     const size_t tb = (idx->nwords + SA_PAD_WORDS) * sizeof(uint64_t);
     const size_t sb = idx->n * (size_t)idx->width;
     const size_t kb = table_entries(idx->depth) * sizeof(uint4);
     const size_t lb = table_entries(idx->depth);
-    const size_t rb = idx->n * 2 * sizeof(uint4);
     if (cudaMalloc(&idx->text, tb) != cudaSuccess || cudaMalloc(&idx->sa, sb) != cudaSuccess ||
-        cudaMalloc(&idx->keys, kb) != cudaSuccess || cudaMalloc(&idx->keylen, lb) != cudaSuccess ||
-        cudaMalloc(&idx->rec, rb) != cudaSuccess) {
+        cudaMalloc(&idx->keys, kb) != cudaSuccess || cudaMalloc(&idx->keylen, lb) != cudaSuccess) {
+        cudaGetLastError();
+        return SA_ERR_NOMEM;
+    }
+    idx->device_bytes = tb + sb + kb + lb;
+    return SA_OK;
+}
+
+int alloc_search_arrays(sa_index *idx) {
+    const size_t rb = idx->n * 2 * sizeof(uint4);
+    if (cudaMalloc(&idx->rec, rb) != cudaSuccess) {
         cudaGetLastError();
         return SA_ERR_NOMEM;
     }
@@ -332,7 +343,7 @@ int alloc_index(sa_index *idx) {
             return SA_ERR_NOMEM;
         }
     }
-    idx->device_bytes = tb + sb + kb + lb + rb + mb;
+    idx->device_bytes += rb + mb;
     return SA_OK;
 }
 
@@ -412,6 +423,9 @@ int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_inde
         }
     }
     st = build_suffix_array(idx, s);
+    cudaStreamSynchronize(s);
+    cudaMemPoolTrimTo(scratch_pool(idx->device), 0);
+    if (st == SA_OK) st = alloc_search_arrays(idx);
     if (st == SA_OK) {
         cudaError_t err = launch_build_keys(idx, s);
         if (err == cudaSuccess) err = launch_build_records(idx, s);
@@ -419,7 +433,6 @@ int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_inde
         if (err == cudaSuccess) err = cudaStreamSynchronize(s);
         st = status_from_cuda(err);
     }
-    cudaMemPoolTrimTo(scratch_pool(idx->device), 0);
     if (st) {
         free_index(idx);
         return st;
@@ -608,6 +621,7 @@ int sa_load(const char *path, void *stream, sa_index **out) {
         return SA_ERR_FORMAT;
     }
     int st = alloc_index(idx);
+    if (st == SA_OK) st = alloc_search_arrays(idx);
     if (st) {
         free_index(idx);
         return st;

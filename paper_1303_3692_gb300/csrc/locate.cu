@@ -5,8 +5,8 @@
 //
 // Three launches: per-tile sums of k_q, one CTA scanning the tile sums, and a
 // CTA per tile that scans its own k_q, writes the offsets and gathers.  Each
-// tile is kTileThreads x kItems consecutive queries; a thread owns kItems
-// consecutive queries.
+// tile is kTileThreads x kItems consecutive queries; thread t of a tile owns
+// queries t, t + kTileThreads, t + 2 kTileThreads, ... of it.
 #include <mutex>
 
 #include "sa_internal.cuh"
@@ -92,38 +92,36 @@ __global__ void __launch_bounds__(1024) scan_partials_kernel(uint64_t *partials,
     if (threadIdx.x == 0) partials[ntiles] = carry_s;
 }
 
+// Item i of thread t covers query tile_base + i * kTileThreads + t (the same
+// queries tile_sums_kernel summed), so every load of results and every store
+// of offsets is coalesced.  Items are scanned in order i = 0..kItems-1.
 template <typename IdxT>
 __global__ void __launch_bounds__(kTileThreads) tile_gather_kernel(const __grid_constant__ LocateLaunch a) {
-    const uint64_t base = (uint64_t)blockIdx.x * kTile + (uint64_t)threadIdx.x * kItems;
-    uint64_t k[kItems];
-    uint64_t s = 0;
-#pragma unroll
-    for (int i = 0; i < kItems; i++) {
-        const uint64_t q = base + i;
-        k[i] = q < a.n_q ? kept(a.res[q], a.cap) : 0;
-        s += k[i];
-    }
-    uint64_t total;
-    uint64_t off = a.partials[blockIdx.x] + block_exclusive_scan(s, &total);
+    const uint64_t tile_base = (uint64_t)blockIdx.x * kTile;
     const uint64_t ntiles = gridDim.x;
     if (blockIdx.x == ntiles - 1 && threadIdx.x == 0) a.out_offsets[a.n_q] = a.partials[ntiles];
+    uint64_t running = a.partials[blockIdx.x];
     IdxT *pos = reinterpret_cast<IdxT *>(a.out_pos);
 #pragma unroll 1
     for (int i = 0; i < kItems; i++) {
-        const uint64_t q = base + i;
-        if (q >= a.n_q) break;
+        const uint64_t q = tile_base + (uint64_t)i * kTileThreads + threadIdx.x;
+        sa_result r{0, 0, 0};
+        if (q < a.n_q) r = a.res[q];
+        const uint64_t k = q < a.n_q ? kept(r, a.cap) : 0;
+        uint64_t total;
+        const uint64_t off = running + block_exclusive_scan(k, &total);
+        running += total;
+        if (q >= a.n_q) continue;
         a.out_offsets[q] = off;
-        if (pos != nullptr && k[i] != 0) {
-            const uint32_t r = a.q_ref ? a.q_ref[q] : 0u;
-            const RefDesc &d = a.refs.r[r < a.n_refs ? r : 0];
+        if (pos != nullptr && k != 0) {
+            const uint32_t ref = a.q_ref ? a.q_ref[q] : 0u;
+            const RefDesc &d = a.refs.r[ref < a.n_refs ? ref : 0];
             const IdxT *sa = reinterpret_cast<const IdxT *>(d.sa);
-            const uint64_t lo = a.res[q].lo;
-            const uint64_t kk = (r < a.n_refs && lo <= d.n && k[i] <= d.n - lo) ? k[i] : 0;  // never read past SA
+            const uint64_t kk = (ref < a.n_refs && r.lo <= d.n && k <= d.n - r.lo) ? k : 0;  // never read past SA
             for (uint64_t t = 0; t < kk; t++) {
-                if (off + t < a.capacity) pos[off + t] = __ldg(sa + lo + t);
+                if (off + t < a.capacity) pos[off + t] = __ldg(sa + r.lo + t);
             }
         }
-        off += k[i];
     }
 }
 

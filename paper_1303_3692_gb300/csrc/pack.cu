@@ -4,16 +4,22 @@
 namespace sa {
 
 // Four ASCII bytes (little-endian in v) to four 2-bit codes in the low byte,
-// first base in the top two bits.  The check: the codes are turned back into
-// the letters A, C, G, T with one byte permutation, and any difference from
-// the case-folded input is ORed into *bad.
+// first base in the top two bits.  Per byte, with u the case-folded byte:
+// x = (u >> 1) & 3 is A0 C1 G3 T2 and c = x ^ (x >> 1) is A0 C1 G2 T3.  The
+// codes sit at bits 0, 8, 16, 24; one multiply by 2^30 + 2^20 + 2^10 + 1
+// moves them to bits 30, 28, 26, 24 without carries between the partial
+// products.  The check rebuilds each letter from its code, 'A' + 2c + 2h +
+// 11 (c & h) with h = c >> 1 (giving A, C, G, T for c = 0..3), and ORs any
+// difference from u into *bad.
 __device__ __forceinline__ uint32_t pack4_fast(uint32_t v, uint32_t *bad) {
     const uint32_t u = v & 0xDFDFDFDFu;
     const uint32_t x = (u >> 1) & 0x03030303u;
-    const uint32_t c = x ^ ((x >> 1) & 0x01010101u);  // per byte: A0 C1 G2 T3
-    const uint32_t sel = (c & 0x3u) | ((c >> 4) & 0x30u) | ((c >> 8) & 0x300u) | ((c >> 12) & 0x3000u);
-    *bad |= u ^ __byte_perm(0x54474341u, 0u, sel);  // bytes 'A','C','G','T' picked by the codes
-    return ((sel & 0x3u) << 6) | (sel & 0x30u) | ((sel >> 6) & 0xCu) | ((sel >> 12) & 0x3u);
+    const uint32_t h0 = (x >> 1) & 0x01010101u;
+    const uint32_t c = x ^ h0;                     // per byte: A0 C1 G2 T3
+    const uint32_t h = (c >> 1) & 0x01010101u;
+    const uint32_t expect = 0x41414141u + 2u * c + 2u * h + 11u * (c & h);
+    *bad |= u ^ expect;
+    return (c * 0x40100401u) >> 24;
 }
 
 // One thread per packed word; words past the text (padding) are zero.
@@ -122,10 +128,10 @@ __global__ void pack_queries_kernel(const __grid_constant__ SearchLaunch a, int 
             const bool range_ok = qa <= qe && qe <= a.total && qe - qa < (1ull << 31);
             if (!range_ok) bad |= 1u;  // inconsistent offsets: the batch is reported invalid
             if (!range_ok || r >= a.n_refs) {
-                a.meta[q] = make_uint4(0u, 0u, kQueryInvalid, 0u);
+                a.meta[2 * q] = make_uint4(0u, 0u, kQueryInvalid, 0u);
                 qa = qe = 0;
             } else if (qe == qa) {
-                a.meta[q] = make_uint4(0xFFFFFFFFu, (uint32_t)a.refs.r[r].n, 0u, 0u);
+                a.meta[2 * q] = make_uint4(0xFFFFFFFFu, (uint32_t)a.refs.r[r].n, 0u, 0u);
             } else {
                 words = (uint32_t)((qe - qa + 31) >> 5);
             }
@@ -159,6 +165,7 @@ __global__ void pack_queries_kernel(const __grid_constant__ SearchLaunch a, int 
                 const uint64_t slot = query_slot(ai, q0 + i);
                 const uint64_t word = pack_word(ascii, a.total, s, nb, &bad);
                 a.qwords[4 * slot + j] = word;
+                uint64_t *mq = reinterpret_cast<uint64_t *>(a.meta + 2 * (q0 + i) + 1);
                 if (j == 0) {
                     const RefDesc &d = a.refs.r[ri];
                     const uint32_t m = (uint32_t)(ei - ai);
@@ -168,7 +175,11 @@ __global__ void pack_queries_kernel(const __grid_constant__ SearchLaunch a, int 
                         L = __ldg(d.kmer + x) - 1u;
                         R = __ldg(d.kmer + x + 1);
                     }
-                    a.meta[q0 + i] = make_uint4(L, R, m, (uint32_t)slot);
+                    a.meta[2 * (q0 + i)] = make_uint4(L, R, m, (uint32_t)slot);
+                    mq[0] = word;
+                    if (ei - ai <= 32) mq[1] = 0;
+                } else if (j == 1) {
+                    mq[1] = word;
                 }
             }
         }

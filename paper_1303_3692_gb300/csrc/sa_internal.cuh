@@ -104,9 +104,11 @@ __device__ __forceinline__ uint32_t base_code(uint32_t c) {
 // First 32-byte slot of a query whose bases start at byte a_rel of the batch.
 __host__ __device__ __forceinline__ uint64_t query_slot(uint64_t a_rel, uint64_t q) { return (a_rel >> 7) + q; }
 
-// Per-query record written by the pack kernel for the search: x, y = the
-// starting bracket (L, R) of the binary search (L = 0xFFFFFFFF for -1), z = m
-// (kQueryInvalid for a query that cannot be searched), w = its first slot.
+// Per-query record written by the pack kernel for the search, 32 bytes (two
+// uint4): x, y = the starting bracket (L, R) of the binary search
+// (L = 0xFFFFFFFF for -1), z = m (kQueryInvalid for a query that cannot be
+// searched), w = its first slot; then the query's first two packed words
+// (bases 0-63), so that the search starts from one sector.
 constexpr uint32_t kQueryInvalid = 0xFFFFFFFFu;
 
 template <typename IdxT>
@@ -175,7 +177,7 @@ struct SearchLaunch {
     uint64_t total;           // q_off[n_q] - q_off[0]: query ranges past it are invalid
     const uint32_t *q_ref;    // null when n_refs == 1
     uint64_t n_q;
-    uint4 *meta;              // n_q per-query records from the pack kernel
+    uint4 *meta;              // 2 n_q uint4: per-query records from the pack kernel
     sa_result *out;
     const int *pack_err;      // device flag: a query had a non-ACGT byte
     unsigned long long *counter;

@@ -223,10 +223,10 @@ __device__ __forceinline__ int cmp_record(uint64_t q0, uint64_t q1, const uint64
 // The search of one query is a sequence of steps, one compare each, run by
 // its lane one step per loop iteration so that the 32 lanes of a warp stay in
 // the same short code path:
-//   init      read the query's record from the pack kernel (length, slot and
-//             starting bracket) and its first 64 bases; when the index has a
-//             k-mer table and m >= k the bracket comes from the table entries
-//             of its first k bases and the descent is skipped;
+//   init      read the query's 32-byte record from the pack kernel (length,
+//             slot, starting bracket and the first 64 bases); when the index
+//             has a k-mer table and m >= k the bracket comes from the table
+//             entries of its first k bases and the descent is skipped;
 //   descent   compare with the key of level-order node k in shared memory
 //             (k = 0 once the table's depth is passed or the bounds split);
 //   deep      load the suffix record of rank M = L + (R - L)/2 (32 bytes: 112
@@ -346,7 +346,8 @@ __global__ void __launch_bounds__(Occ<kOcc>::threads, Occ<kOcc>::blocks)
 
         if (fresh) {
             fresh = false;
-            const uint4 mt = __ldg(a.meta + q);
+            const uint4 mt = __ldg(a.meta + 2 * (size_t)q);
+            const uint4 mw = __ldg(a.meta + 2 * (size_t)q + 1);
             const uint32_t r = (!kSingle && a.q_ref) ? __ldg(a.q_ref + q) : 0u;
             if (bad_batch || mt.z == kQueryInvalid || r >= a.n_refs) {
                 write_result(a.out, q, ~0ull, ~0ull);
@@ -371,9 +372,8 @@ __global__ void __launch_bounds__(Occ<kOcc>::threads, Occ<kOcc>::blocks)
                 continue;
             }
             Q = a.qwords + 4 * (size_t)mt.w;
-            const ulonglong2 qw = __ldg(reinterpret_cast<const ulonglong2 *>(Q));
-            q0 = qw.x;
-            q1 = qw.y;
+            q0 = ((uint64_t)mw.y << 32) | mw.x;
+            q1 = ((uint64_t)mw.w << 32) | mw.z;
             lcpL = lcpR = 0;
             phase = 0;
             L = mt.x;  // the pack kernel's bracket: the k-mer table's, or [-1, n)

@@ -244,31 +244,38 @@ MULTI_REF_GC = (0.38, 0.45, 0.50, 0.62)
 def multi_genome(scale: float = 1.0, seed: int = SEED0 + 3):
     """4 references (5, 12, 25, 50 Mbp; GC 0.38/0.45/0.50/0.62; 5% segmental
     duplications) and 16,000,000 queries of length U[20,250], each assigned
-    uniformly to one reference, 70% sampled from it and 30% random.
-    Returns (refs, q_bases, q_offsets, q_ref, sampled)."""
+    uniformly to one reference, 70% sampled from it (no substitutions) and 30%
+    random.  Returns (refs, q_bases, q_offsets, q_ref, sampled)."""
     refs = [reference(max(2_000, int(s * scale)), seed + 10 * i, gc=g, sd_cover=0.05)
             for i, (s, g) in enumerate(zip(MULTI_REF_SIZES, MULTI_REF_GC))]
     nq = max(4, int(16_000_000 * scale))
     rng = _rng(seed + 999)
+    mmin, mmax = 20, 250
     q_ref = rng.integers(0, len(refs), nq).astype(np.uint32)
-    parts = []
-    for r in range(len(refs)):
-        idx = np.nonzero(q_ref == r)[0]
-        qb, qo, smp = queries(refs[r], idx.size, seed + 1000 + r, m=(20, 250),
-                              frac_sampled=0.7, subs=(0, 0))
-        parts.append((idx, qb, qo, smp))
-    lens = np.zeros(nq, dtype=np.int64)
-    sampled = np.zeros(nq, dtype=bool)
-    for idx, qb, qo, smp in parts:
-        lens[idx] = np.diff(qo)
-        sampled[idx] = smp
+    lens = rng.integers(mmin, mmax + 1, nq).astype(np.int64)
+    sampled = rng.random(nq) < 0.7
     offsets = np.zeros(nq + 1, dtype=np.int64)
     np.cumsum(lens, out=offsets[1:])
     bases = np.empty(int(offsets[-1]), dtype=np.uint8)
-    for idx, qb, qo, smp in parts:
-        # scatter each reference's queries into their global slots
-        src_len = np.diff(qo)
-        rows = np.repeat(idx, src_len)
-        within = np.arange(qb.size) - np.repeat(qo[:-1], src_len)
-        bases[offsets[rows] + within] = qb
+    # all references back to back; a sampled query of reference r starts
+    # uniformly in [base_r, base_r + n_r - m] and never crosses into the next
+    cat = np.concatenate(refs)
+    starts_r = np.zeros(len(refs) + 1, dtype=np.int64)
+    np.cumsum([r.size for r in refs], out=starts_r[1:])
+    win = np.lib.stride_tricks.sliding_window_view(cat, mmax)
+    step = 1 << 20
+    for s in range(0, nq, step):
+        e = min(nq, s + step)
+        k = e - s
+        L = lens[s:e]
+        r = q_ref[s:e]
+        blk = ASCII[rng.integers(0, 4, (k, mmax), dtype=np.uint8)]
+        smp = sampled[s:e]
+        n_r = (starts_r[r + 1] - starts_r[r])
+        room = np.maximum(n_r - L + 1, 1)
+        st = starts_r[r] + (rng.random(k) * room).astype(np.int64)
+        st = np.minimum(st, cat.size - mmax)  # a window of mmax must fit; only bases < L are kept
+        blk[smp] = win[st[smp]]
+        mask = np.arange(mmax)[None, :] < L[:, None]
+        bases[offsets[s]:offsets[e]] = blk[mask]
     return refs, bases, offsets, q_ref, sampled

@@ -66,3 +66,30 @@ def test_plain_kernel_full_size_sample(c2):
     a = sa.sa_search_batch(idx, qb, qo).cpu()
     b = sa.sa_search_batch_plain(idx, qb, qo).cpu()
     assert torch.equal(a, b)
+
+
+def test_multi_genome_full_size():
+    """4 references (5, 12, 25, 50 Mbp) and 16,000,000 queries of U[20,250] bp,
+    each assigned to one reference, searched in one call with q_ref: every
+    query's interval equals the oracle's on its own reference."""
+    from paper_1303_3692_gb300 import build_lib, sa
+
+    build_lib.build()
+    refs, qb, qo, qref, smp = datagen.multi_genome()
+    idxs = [sa.sa_build(torch.from_numpy(r).cuda()) for r in refs]
+    got = sa.sa_search_batch(idxs, torch.from_numpy(qb).cuda(), torch.from_numpy(qo).cuda(),
+                             q_ref=torch.from_numpy(qref).cuda()).cpu().numpy()
+    for r, ref in enumerate(refs):
+        T = oracle.normalize(ref)
+        osa = oracle.sa_naive(T)
+        assert np.array_equal(idxs[r].suffix_array().cpu().numpy().astype(np.int64), osa)
+        sel = np.nonzero(qref == r)[0]
+        lens = qo[sel + 1] - qo[sel]
+        sub_qo = np.zeros(sel.size + 1, dtype=np.int64)
+        np.cumsum(lens, out=sub_qo[1:])
+        # gather this reference's queries into one contiguous buffer
+        idx = np.repeat(qo[sel], lens) + (np.arange(int(lens.sum())) - np.repeat(sub_qo[:-1], lens))
+        lo, hi = oracle.search_batch(T, osa, qb[idx], sub_qo, threads=oracle.cpu_threads())
+        assert np.array_equal(got[sel, 0], lo), r
+        assert np.array_equal(got[sel, 1], hi), r
+        assert np.array_equal(got[sel, 2], hi - lo), r
