@@ -137,18 +137,19 @@ int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_inde
  *             may be non-zero; query i is q_bases[q_offsets[i] .. q_offsets[i+1]).
  *             Only the first and last entry are read on the host (with one
  *             small synchronous copy when the array is in device memory,
- *             unless sa_search_batch_ex is given SA_PARAM_Q_RANGE); a query
- *             whose range is inconsistent with them is reported like a
- *             non-ACGT byte.
+ *             unless sa_search_batch_ex is given SA_PARAM_Q_RANGE).
  *  q_ref      n_q reference ids (< n_refs), or NULL when n_refs == 1.
  *  n_q        number of queries, < 2^32 (0 is allowed and does nothing).
  *  out        n_q results (host or device).
  *  stream     CUDA stream or NULL.
  *
- * Errors: SA_ERR_ARG (also for an out-of-range q_ref, detected on the device
- * and reported for the call when the output is on the host, else left as
- * lo = hi = count = UINT64_MAX for that query), SA_ERR_BASE (same rule),
- * SA_ERR_NOMEM, SA_ERR_CUDA.
+ * A query that cannot be searched -- a byte outside {A,C,G,T,a,c,g,t}, an
+ * out-of-range q_ref, or offsets inconsistent with the batch's range -- gets
+ * lo = hi = count = UINT64_MAX; the other queries are unaffected.  When the
+ * output is in host memory the call also reports it: SA_ERR_BASE for a byte
+ * or range problem, else SA_ERR_ARG for a reference id.
+ *
+ * Errors: SA_ERR_ARG, SA_ERR_BASE (see above), SA_ERR_NOMEM, SA_ERR_CUDA.
  */
 int sa_search_batch(const sa_index *const *refs, uint32_t n_refs, const char *q_bases,
                     const uint64_t *q_offsets, const uint32_t *q_ref, uint64_t n_q,

@@ -231,6 +231,7 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     if (nslots >= (1ull << 32)) return SA_ERR_ARG;
     uint64_t *qwords = sc.get<uint64_t>(4 * nslots);
     uint4 *meta = sc.get<uint4>(2 * n_q);
+    uint8_t *qbad = sc.get<uint8_t>(n_q);
     int *flags = sc.get<int>(4);  // [0] pack error, [1] status
     unsigned long long *counter = sc.get<unsigned long long>(1);
     if (sc.failed) return SA_ERR_NOMEM;
@@ -244,8 +245,9 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     const uint32_t threads = params && params->threads_per_block ? params->threads_per_block : 1024;
     const uint32_t bps = params && params->blocks_per_sm ? params->blocks_per_sm : 1;
     if (threads < 32 || threads > 1024 || threads % 32 || bps == 0 || threads * bps > 2048) return SA_ERR_ARG;
-    // shared memory per SM is 228 KB; each CTA also holds ~3 KB of descriptors
-    const uint32_t budget = (kSmemBudget < 224u * 1024u / bps ? kSmemBudget : 224u * 1024u / bps) - 4096u;
+    // shared memory per SM is 228 KB; each CTA also holds ~4 KB of descriptors
+    const uint32_t per_cta = 224u * 1024u / bps - 6144u;
+    const uint32_t budget = per_cta < kSmemBudget ? per_cta : kSmemBudget;
     const uint32_t want_depth = params && params->key_depth ? params->key_depth : kDefaultDepth;
     L.smem_bytes = fill_ref_table(refs, n_refs, plain ? 0 : want_depth, &L.refs, budget);
     L.n_refs = n_refs;
@@ -258,6 +260,7 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     L.q_ref = ref_d;
     L.n_q = n_q;
     L.meta = meta;
+    L.qbad = qbad;
     L.out = out_d;
     L.pack_err = flags;
     L.counter = counter;

@@ -3,25 +3,6 @@
 
 namespace sa {
 
-// Four ASCII bytes (little-endian in v) to four 2-bit codes in the low byte,
-// first base in the top two bits.  Per byte, with u the case-folded byte:
-// x = (u >> 1) & 3 is A0 C1 G3 T2 and c = x ^ (x >> 1) is A0 C1 G2 T3.  The
-// codes sit at bits 0, 8, 16, 24; one multiply by 2^30 + 2^20 + 2^10 + 1
-// moves them to bits 30, 28, 26, 24 without carries between the partial
-// products.  The check rebuilds each letter from its code, 'A' + 2c + 2h +
-// 11 (c & h) with h = c >> 1 (giving A, C, G, T for c = 0..3), and ORs any
-// difference from u into *bad.
-__device__ __forceinline__ uint32_t pack4_fast(uint32_t v, uint32_t *bad) {
-    const uint32_t u = v & 0xDFDFDFDFu;
-    const uint32_t x = (u >> 1) & 0x03030303u;
-    const uint32_t h0 = (x >> 1) & 0x01010101u;
-    const uint32_t c = x ^ h0;                     // per byte: A0 C1 G2 T3
-    const uint32_t h = (c >> 1) & 0x01010101u;
-    const uint32_t expect = 0x41414141u + 2u * c + 2u * h + 11u * (c & h);
-    *bad |= u ^ expect;
-    return (c * 0x40100401u) >> 24;
-}
-
 // One thread per packed word; words past the text (padding) are zero.
 __global__ void pack_text_kernel(const uint8_t *__restrict__ ascii, uint64_t n, uint64_t *__restrict__ words,
                                  uint64_t nwords_padded, int *err_flag, bool aligned16) {
@@ -66,57 +47,21 @@ cudaError_t launch_pack_text(const char *ascii, uint64_t n, uint64_t *words, uin
     return cudaGetLastError();
 }
 
-// Packs 32 ASCII bases starting at byte s of a (nb <= 32 bytes belong to the
-// query; the rest pack as A).  When nine aligned 32-bit words around them lie
-// inside [a, a + total) they are read and aligned with funnel shifts, and the
-// bases past nb are masked to A afterwards; those bytes belong to the next
-// query, which checks them itself.  Only the batch's last word takes the
-// byte loop.
-__device__ __forceinline__ uint64_t pack_word(const uint8_t *__restrict__ a, uint64_t total, uint64_t s,
-                                              uint32_t nb, uint32_t *bad) {
-    const uintptr_t lo_addr = ((uintptr_t)(a + s)) & ~(uintptr_t)3;
-    uint64_t word = 0;
-    if (lo_addr >= (uintptr_t)a && lo_addr + 36 <= (uintptr_t)(a + total)) {
-        const uint32_t *p = reinterpret_cast<const uint32_t *>(lo_addr);
-        const uint32_t sh = (uint32_t)(((uintptr_t)(a + s)) & 3u) * 8u;
-        uint32_t v[9];
-#pragma unroll
-        for (int i = 0; i < 9; i++) v[i] = __ldg(p + i);
-        uint32_t hi = 0, lo = 0;
-#pragma unroll
-        for (int i = 0; i < 4; i++) hi = (hi << 8) | pack4_fast(__funnelshift_r(v[i], v[i + 1], sh), bad);
-#pragma unroll
-        for (int i = 4; i < 8; i++) lo = (lo << 8) | pack4_fast(__funnelshift_r(v[i], v[i + 1], sh), bad);
-        word = ((uint64_t)hi << 32) | lo;
-        if (nb < 32) word &= ~0ull << (64u - 2u * nb);
-    } else {
-        for (uint32_t j = 0; j < 32; j++) {
-            uint32_t code = 0;
-            if (j < nb) {
-                code = base_code(a[s + j]);
-                if (code > 3) {
-                    *bad |= 1u;
-                    code = 0;
-                }
-            }
-            word = (word << 2) | code;
-        }
-    }
-    return word;
-}
-
-// Each warp takes 32 consecutive queries (one per lane), scans their word
-// counts, and then packs one output word per lane per round: a round covers
-// 32 consecutive 32-base words of the batch, so the lanes read one
-// contiguous kilobyte.  The lane that packs a query's first word also writes
-// the query's record for the search: the bracket from the reference's k-mer
-// table when m >= k, else the whole range [-1, n).
+// Packs every query and writes its record for the search.  Each warp takes
+// 32 consecutive queries (one per lane), scans their word counts, and then
+// packs one output word per lane per round: a round covers 32 consecutive
+// 32-base words of the batch, so the lanes read one contiguous kilobyte.
+// Every word goes to the query's 32-byte slots; the lane that packs a
+// query's first word also writes the first part of its record (the bracket
+// from the reference's k-mer table when m >= k, else [-1, n); m; the slot)
+// and the first two words go to the record's second half.  A query with a
+// byte outside {A,C,G,T,a,c,g,t} gets qbad[q] = 1.
 __global__ void pack_queries_kernel(const __grid_constant__ SearchLaunch a, int *err_flag) {
     const unsigned lane = threadIdx.x & 31u;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint8_t *ascii = reinterpret_cast<const uint8_t *>(a.ascii);
-    uint32_t bad = 0;
+    bool any_bad = false;
     for (uint64_t q0 = warp * 32; q0 < a.n_q; q0 += nwarps * 32) {
         const uint64_t q = q0 + lane;
         uint64_t qa = 0, qe = 0;
@@ -126,7 +71,8 @@ __global__ void pack_queries_kernel(const __grid_constant__ SearchLaunch a, int 
             qe = __ldg(a.q_off + q + 1) - a.first;
             r = a.q_ref ? __ldg(a.q_ref + q) : 0u;
             const bool range_ok = qa <= qe && qe <= a.total && qe - qa < (1ull << 31);
-            if (!range_ok) bad |= 1u;  // inconsistent offsets: the batch is reported invalid
+            a.qbad[q] = 0;
+            if (!range_ok) any_bad = true;  // inconsistent offsets: this query is invalid
             if (!range_ok || r >= a.n_refs) {
                 a.meta[2 * q] = make_uint4(0u, 0u, kQueryInvalid, 0u);
                 qa = qe = 0;
@@ -144,10 +90,10 @@ __global__ void pack_queries_kernel(const __grid_constant__ SearchLaunch a, int 
         }
         const uint32_t excl = incl - words;
         const uint32_t W = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        __syncwarp();
         for (uint32_t base = 0; base < W; base += 32) {
             const uint32_t t = base + lane;
-            // owner: the last lane whose first word is <= t
-            uint32_t i = 0;
+            uint32_t i = 0;  // owner: the last lane whose first word is <= t
 #pragma unroll
             for (uint32_t b = 16; b > 0; b >>= 1) {
                 const uint32_t ex = __shfl_sync(0xFFFFFFFFu, excl, i + b);
@@ -163,6 +109,7 @@ __global__ void pack_queries_kernel(const __grid_constant__ SearchLaunch a, int 
                 const uint64_t left = ei - s;
                 const uint32_t nb = left < 32 ? (uint32_t)left : 32u;
                 const uint64_t slot = query_slot(ai, q0 + i);
+                uint32_t bad = 0;
                 const uint64_t word = pack_word(ascii, a.total, s, nb, &bad);
                 a.qwords[4 * slot + j] = word;
                 uint64_t *mq = reinterpret_cast<uint64_t *>(a.meta + 2 * (q0 + i) + 1);
@@ -181,10 +128,14 @@ __global__ void pack_queries_kernel(const __grid_constant__ SearchLaunch a, int 
                 } else if (j == 1) {
                     mq[1] = word;
                 }
+                if (bad) {
+                    a.qbad[q0 + i] = 1;
+                    any_bad = true;
+                }
             }
         }
     }
-    if (__any_sync(0xFFFFFFFFu, bad != 0) && lane == 0) atomicOr(err_flag, 1);
+    if (__any_sync(0xFFFFFFFFu, any_bad) && lane == 0) atomicOr(err_flag, 1);
 }
 
 cudaError_t launch_pack_queries(const SearchLaunch &L, int *err_flag, cudaStream_t s) {

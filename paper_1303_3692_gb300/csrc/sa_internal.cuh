@@ -111,6 +111,72 @@ __host__ __device__ __forceinline__ uint64_t query_slot(uint64_t a_rel, uint64_t
 // (bases 0-63), so that the search starts from one sector.
 constexpr uint32_t kQueryInvalid = 0xFFFFFFFFu;
 
+// Four ASCII bytes (little-endian in v) to four 2-bit codes in the low byte,
+// first base in the top two bits.  Per byte, with u the case-folded byte:
+// x = (u >> 1) & 3 is A0 C1 G3 T2 and c = x ^ (x >> 1) is A0 C1 G2 T3.  The
+// codes sit at bits 0, 8, 16, 24; one multiply by 2^30 + 2^20 + 2^10 + 1
+// moves them to bits 30, 28, 26, 24 without carries between the partial
+// products.  The check rebuilds each letter from its code, 'A' + 2c + 2h +
+// 11 (c & h) with h = c >> 1 (giving A, C, G, T for c = 0..3), and ORs any
+// difference from u into *bad.
+__device__ __forceinline__ uint32_t pack4_fast(uint32_t v, uint32_t *bad) {
+    const uint32_t u = v & 0xDFDFDFDFu;
+    const uint32_t x = (u >> 1) & 0x03030303u;
+    const uint32_t h0 = (x >> 1) & 0x01010101u;
+    const uint32_t c = x ^ h0;                     // per byte: A0 C1 G2 T3
+    const uint32_t h = (c >> 1) & 0x01010101u;
+    const uint32_t expect = 0x41414141u + 2u * c + 2u * h + 11u * (c & h);
+    *bad |= u ^ expect;
+    return (c * 0x40100401u) >> 24;
+}
+
+// Packs the 32 ASCII bases starting at byte s of a (the first nb <= 32 belong
+// to the query; the rest pack as A).  When nine aligned 32-bit words around
+// them lie inside [a, a + total) they are read and aligned with funnel
+// shifts; the check covers only the query's own nb bytes.  Otherwise (the
+// batch's last bytes) the bytes are read one at a time.  Returns the word;
+// *bad becomes non-zero if one of the nb bytes is not a base.
+__device__ __forceinline__ uint64_t pack_word(const uint8_t *__restrict__ a, uint64_t total, uint64_t s,
+                                              uint32_t nb, uint32_t *bad) {
+    const uintptr_t lo_addr = ((uintptr_t)(a + s)) & ~(uintptr_t)3;
+    uint64_t word = 0;
+    if (lo_addr >= (uintptr_t)a && lo_addr + 36 <= (uintptr_t)(a + total)) {
+        const uint32_t *p = reinterpret_cast<const uint32_t *>(lo_addr);
+        const uint32_t sh = (uint32_t)(((uintptr_t)(a + s)) & 3u) * 8u;
+        uint32_t v[9];
+#pragma unroll
+        for (int i = 0; i < 9; i++) v[i] = __ldg(p + i);
+        uint32_t hi = 0, lo = 0, b = 0;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            uint32_t gb = 0;
+            const uint32_t g = pack4_fast(__funnelshift_r(v[i], v[i + 1], sh), &gb);
+            const int own = (int)nb - 4 * i;  // bytes of this group that belong to the query
+            b |= own >= 4 ? gb : (own > 0 ? gb & ((1u << (8 * own)) - 1u) : 0u);
+            if (i < 4)
+                hi = (hi << 8) | g;
+            else
+                lo = (lo << 8) | g;
+        }
+        *bad |= b;
+        word = ((uint64_t)hi << 32) | lo;
+        if (nb < 32) word &= ~0ull << (64u - 2u * nb);
+    } else {
+        for (uint32_t j = 0; j < 32; j++) {
+            uint32_t code = 0;
+            if (j < nb) {
+                code = base_code(a[s + j]);
+                if (code > 3) {
+                    *bad |= 1u;
+                    code = 0;
+                }
+            }
+            word = (word << 2) | code;
+        }
+    }
+    return word;
+}
+
 template <typename IdxT>
 __device__ __forceinline__ uint64_t sa_at(const void *sa, uint64_t i) {
     return (uint64_t)__ldg(reinterpret_cast<const IdxT *>(sa) + i);
@@ -177,12 +243,13 @@ struct SearchLaunch {
     uint64_t total;           // q_off[n_q] - q_off[0]: query ranges past it are invalid
     const uint32_t *q_ref;    // null when n_refs == 1
     uint64_t n_q;
-    uint4 *meta;              // 2 n_q uint4: per-query records from the pack kernel
+    uint4 *meta;              // 2 n_q uint4: per-query records written by the pack kernel
+    uint8_t *qbad;            // n_q flags from the pack kernel: the query has a non-base byte
     sa_result *out;
-    const int *pack_err;      // device flag: a query had a non-ACGT byte
+    int *pack_err;            // device flag: some query had a non-ACGT byte or bad offsets
     unsigned long long *counter;
     int *status;
-    uint32_t smem_bytes;
+    uint32_t smem_bytes;      // shared-memory key tables
     uint32_t threads, blocks, chunk;
 };
 cudaError_t launch_search(const SearchLaunch &L, cudaStream_t s);

@@ -294,7 +294,6 @@ __global__ void __launch_bounds__(Occ<kOcc>::threads, Occ<kOcc>::blocks)
 
     const unsigned lane = tid & 31u;
     const unsigned lanemask_lt = (1u << lane) - 1u;
-    const bool bad_batch = a.pack_err != nullptr && *(volatile const int *)a.pack_err != 0;
 
     // Reference fields: uniform registers for one reference, else per lane.
     const SmemDesc d0 = sdesc[0];
@@ -349,7 +348,7 @@ __global__ void __launch_bounds__(Occ<kOcc>::threads, Occ<kOcc>::blocks)
             const uint4 mt = __ldg(a.meta + 2 * (size_t)q);
             const uint4 mw = __ldg(a.meta + 2 * (size_t)q + 1);
             const uint32_t r = (!kSingle && a.q_ref) ? __ldg(a.q_ref + q) : 0u;
-            if (bad_batch || mt.z == kQueryInvalid || r >= a.n_refs) {
+            if (mt.z == kQueryInvalid || a.qbad[q] != 0 || r >= a.n_refs) {
                 write_result(a.out, q, ~0ull, ~0ull);
                 active = false;
                 continue;
@@ -468,7 +467,7 @@ __global__ void __launch_bounds__(256) search_plain_kernel(const __grid_constant
     const uint64_t a0 = __ldg(a.q_off + q) - a.first;
     const uint64_t a1 = __ldg(a.q_off + q + 1) - a.first;
     const uint32_t r = a.q_ref ? __ldg(a.q_ref + q) : 0u;
-    const bool bad = a.pack_err != nullptr && *(volatile const int *)a.pack_err != 0;
+    const bool bad = a.qbad[q] != 0;
     if (bad || r >= a.n_refs || a1 < a0 || a1 > a.total || a1 - a0 >= (1ull << 31)) {
         write_result(a.out, q, ~0ull, ~0ull);
         return;
