@@ -81,7 +81,9 @@ bool on_device(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Scratch allocations released on the stream when the call returns.
+// Scratch allocations released on the stream when the call returns.  Every
+// block is returned 256-byte aligned (kernels read 32-byte records with one
+// 256-bit load), whatever alignment the pool itself guarantees.
 struct Scratch {
     cudaStream_t s;
     std::vector<void *> ptrs;
@@ -90,13 +92,14 @@ struct Scratch {
     T *get(size_t count) {
         void *p = nullptr;
         if (failed) return nullptr;
-        if (scratch_alloc(&p, count * sizeof(T) + 16, s) != cudaSuccess) {
+        if (scratch_alloc(&p, count * sizeof(T) + 256 + 16, s) != cudaSuccess) {
             failed = true;
             cudaGetLastError();
             return nullptr;
         }
         ptrs.push_back(p);
-        return reinterpret_cast<T *>(p);
+        const uintptr_t a = ((uintptr_t)p + 255) & ~(uintptr_t)255;
+        return reinterpret_cast<T *>(a);
     }
     ~Scratch() {
         for (void *p : ptrs) scratch_free(p, s);
@@ -231,7 +234,7 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     if (nslots >= (1ull << 32)) return SA_ERR_ARG;
     uint64_t *qwords = sc.get<uint64_t>(4 * nslots);
     uint4 *meta = sc.get<uint4>(2 * n_q);
-    uint8_t *qbad = sc.get<uint8_t>(n_q);
+    if (((uintptr_t)meta & 31u) != 0) return SA_ERR_CUDA;  // the search reads 32-byte records
     int *flags = sc.get<int>(4);  // [0] pack error, [1] status
     unsigned long long *counter = sc.get<unsigned long long>(1);
     if (sc.failed) return SA_ERR_NOMEM;
@@ -260,7 +263,6 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     L.q_ref = ref_d;
     L.n_q = n_q;
     L.meta = meta;
-    L.qbad = qbad;
     L.out = out_d;
     L.pack_err = flags;
     L.counter = counter;

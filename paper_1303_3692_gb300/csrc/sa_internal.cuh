@@ -177,6 +177,16 @@ __device__ __forceinline__ uint64_t pack_word(const uint8_t *__restrict__ a, uin
     return word;
 }
 
+// One 32-byte (one DRAM sector) read-only load; p must be 32-byte aligned.
+// A single request per sector instead of two 16-byte ones, which the memory
+// system would otherwise serve as two misses.
+__device__ __forceinline__ void ldg32(const void *p, uint4 *lo, uint4 *hi) {
+    unsigned long long a, b, c, d;
+    asm volatile("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+    *lo = make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
+    *hi = make_uint4((uint32_t)c, (uint32_t)(c >> 32), (uint32_t)d, (uint32_t)(d >> 32));
+}
+
 template <typename IdxT>
 __device__ __forceinline__ uint64_t sa_at(const void *sa, uint64_t i) {
     return (uint64_t)__ldg(reinterpret_cast<const IdxT *>(sa) + i);
@@ -244,7 +254,6 @@ struct SearchLaunch {
     const uint32_t *q_ref;    // null when n_refs == 1
     uint64_t n_q;
     uint4 *meta;              // 2 n_q uint4: per-query records written by the pack kernel
-    uint8_t *qbad;            // n_q flags from the pack kernel: the query has a non-base byte
     sa_result *out;
     int *pack_err;            // device flag: some query had a non-ACGT byte or bad offsets
     unsigned long long *counter;

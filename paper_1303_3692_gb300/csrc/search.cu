@@ -345,10 +345,10 @@ __global__ void __launch_bounds__(Occ<kOcc>::threads, Occ<kOcc>::blocks)
 
         if (fresh) {
             fresh = false;
-            const uint4 mt = __ldg(a.meta + 2 * (size_t)q);
-            const uint4 mw = __ldg(a.meta + 2 * (size_t)q + 1);
+            uint4 mt, mw;
+            ldg32(a.meta + 2 * (size_t)q, &mt, &mw);
             const uint32_t r = (!kSingle && a.q_ref) ? __ldg(a.q_ref + q) : 0u;
-            if (mt.z == kQueryInvalid || a.qbad[q] != 0 || r >= a.n_refs) {
+            if (mt.z == kQueryInvalid || r >= a.n_refs) {
                 write_result(a.out, q, ~0ull, ~0ull);
                 active = false;
                 continue;
@@ -405,8 +405,8 @@ __global__ void __launch_bounds__(Occ<kOcc>::threads, Occ<kOcc>::blocks)
             k = (c == CMP_PREFIX || nk >= (1u << depth)) ? 0u : nk;
         } else {
             M = L + ((R - L) >> 1);
-            const uint4 r0 = __ldg(REC + 2 * (size_t)M);
-            const uint4 r1 = __ldg(REC + 2 * (size_t)M + 1);
+            uint4 r0, r1;
+            ldg32(REC + 2 * (size_t)M, &r0, &r1);
             bool und = false;
             c = cmp_record(q0, q1, Q, m, r0, r1, n, &l, &und);
             if (und) c = cmp_suffix32(T, n, r1.w, Q, m, max(112u, min(lcpL, lcpR)), &l);
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(256) search_plain_kernel(const __grid_constant
     const uint64_t a0 = __ldg(a.q_off + q) - a.first;
     const uint64_t a1 = __ldg(a.q_off + q + 1) - a.first;
     const uint32_t r = a.q_ref ? __ldg(a.q_ref + q) : 0u;
-    const bool bad = a.qbad[q] != 0;
+    const bool bad = a.meta[2 * q].z == kQueryInvalid;
     if (bad || r >= a.n_refs || a1 < a0 || a1 > a.total || a1 - a0 >= (1ull << 31)) {
         write_result(a.out, q, ~0ull, ~0ull);
         return;

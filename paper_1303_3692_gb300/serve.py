@@ -49,8 +49,8 @@ class Request:
 
 def scratch_bytes(n_q: int, n_bases: int) -> int:
     """Device scratch one search call takes from the library's pool: packed
-    query slots, 32-byte per-query records, per-query flags and small flags."""
-    return 32 * ((n_bases >> 7) + n_q + 1) + 33 * n_q + 64
+    query slots, 32-byte per-query records and small flags."""
+    return 32 * ((n_bases >> 7) + n_q + 1) + 32 * n_q + 64
 
 
 def form_batch(queue: List[Request], max_q: int, max_bases: int, budget: int):
