@@ -52,9 +52,10 @@ KERNEL_BYTES_PER_QUERY = {
 }
 BYTES_SOURCE = "oracle/bytes_model.py --workload repetitive-100m (k = 14)"
 
-# DRAM bytes per search-kernel launch from one ncu capture, valid only while
-# the kernel sources hash to KERNEL_SHA (else reported as null).
-TRAFFIC = {"kernel_sha": None, "kernel": None, "dram_bytes_per_launch": None}
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture (--set full, 100 Mbp workload), valid only while the kernel sources
+# hash to kernel_sha (else reported as null).
+TRAFFIC = {"kernel_sha": "04ffe1e61dcee4bb", "kernel": "pack_queries_kernel", "dram_bytes_per_launch": 2345388000 + 624944128}
 
 
 def kernel_sha() -> str:
