@@ -35,32 +35,39 @@ METRIC = "exact-match queries/s (query bases/s, % HBM roofline alongside)"
 UNIT = "queries/s"
 WORKLOAD = "repetitive-100Mbp-10M-q100-locate64"
 
-# Algorithmic bytes per query of each kernel of a step on this workload
+# Algorithmic bytes per query of each phase of a step on this workload
 # (m = 100, k = 14), from the oracle's byte model (oracle/bytes_model.py:
-# oracle_probe_model_kmer on 20,000 seeded queries: 1.19375 record probes and
-# 6.58 occurrences per query on average, 0.51 positions kept at cap 64):
-#   pack_queries_kernel: 100 ASCII bytes read + 8 offset bytes + one 32-byte
-#       k-mer table sector + 25 packed bytes written          = 165.0
-#   search_kernel: 25 packed query bytes + 32 per record probe + 12 result
-#       bytes (lo, hi, count at the suffix array's width)      = 75.2
+# oracle_probe_model_kmer on 20,000 seeded queries: 1.19375 record probes per
+# query, 0.41265 of them after the one that comes with the 64-byte k-mer entry,
+# 6.58 occurrences on average, 0.51 positions kept at cap 64):
+#   pack_batch_kernel: 100 ASCII bytes read + 25 packed bytes and 12.5 bytes of
+#       per-base validity masks written                         = 137.5
+#   search (front_kernel + search_kernel): 8 offset bytes + 25 packed query
+#       bytes + 12.5 validity bytes + one 64-byte k-mer entry + 32 per further
+#       record probe + 12 result bytes (lo, hi, count at the suffix array's
+#       width)                                                  = 134.7
 #   locate (3 kernels): 24 result bytes read + 8 offset bytes written + 4.1
 #       position bytes (suffix-array entry read and written)   = 36.1
 KERNEL_BYTES_PER_QUERY = {
-    "pack_queries_kernel": 100 + 8 + 32 + 25,
-    "search_kernel": 25 + 32 * 1.19375 + 12,
+    "pack_batch_kernel": 100 + 25 + 12.5,
+    "search": 8 + 25 + 12.5 + 64 + 32 * 0.41265 + 12,
     "locate": 24 + 8 + 4.1072,
 }
+# Random DRAM accesses per query of the search phase (the k-mer entry, further
+# record probes, text windows), from the same model: random 32- or 64-byte
+# reads are bounded by the DRAM's row activations, not by its bandwidth.
+RANDOM_ACCESSES_PER_QUERY = {"search": 1.41265}
 BYTES_SOURCE = "oracle/bytes_model.py --workload repetitive-100m (k = 14)"
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture (--set full, 100 Mbp workload), valid only while the kernel sources
 # hash to kernel_sha (else reported as null).
-TRAFFIC = {"kernel_sha": "04ffe1e61dcee4bb", "kernel": "pack_queries_kernel", "dram_bytes_per_launch": 2345388000 + 624944128}
+TRAFFIC = {"kernel_sha": None, "kernel": None, "dram_bytes_per_launch": None}
 
 
 def kernel_sha() -> str:
     h = hashlib.sha256()
-    for f in ("search.cu", "pack.cu", "locate.cu", "sa_internal.cuh"):
+    for f in ("search.cu", "front.cu", "pack.cu", "locate.cu", "sa_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1303_3692_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -144,24 +151,16 @@ def build_workload(scale: float):
     return datagen.repetitive_100m(scale=scale)
 
 
-def run_multi_genome(args, world, rank, local):
-    """4 references (5, 12, 25, 50 Mbp) and 16,000,000 queries of U[20,250] bp
-    in one multi-reference call (count only); the launch shape is autotuned."""
+def _time_count_steps(idxs, qb_d, qo_d, qr_d, params, args, local):
+    """Times args.steps count-only searches (warm-up first, L2 flushed before
+    each step): (step ms list, search-kernel ms list, clock summary)."""
     import torch
 
     import paper_1303_3692_gb300.sa as sa
-    from paper_1303_3692_gb300 import autotune, datagen
 
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    refs, qb, qo, qref, _ = datagen.multi_genome(scale=args.scale)
-    t0 = time.perf_counter()
-    idxs = [sa.sa_build(torch.from_numpy(r).to(dev)) for r in refs]
-    build_s = time.perf_counter() - t0
-    n_q = qo.size - 1
-    qb_d, qo_d, qr_d = (torch.from_numpy(x).to(dev) for x in (qb, qo, qref))
+    dev = qb_d.device
+    n_q = qo_d.numel() - 1
     out = torch.empty((n_q, 3), dtype=torch.int64, device=dev)
-    params, tune = autotune.autotune(idxs, qb_d, qo_d, q_ref=qr_d, use_cache=False)
     stream = torch.cuda.current_stream()
 
     def lib_event():
@@ -170,7 +169,7 @@ def run_multi_genome(args, world, rank, local):
         return e
 
     params.flags = sa.SA_PARAM_Q_RANGE
-    params.q_first, params.q_total = 0, int(qo[-1])
+    params.q_first, params.q_total = 0, int(qo_d[-1].item())
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
         sa.sa_search_batch(idxs, qb_d, qo_d, q_ref=qr_d, out=out, params=params)
@@ -189,6 +188,27 @@ def run_multi_genome(args, world, rank, local):
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     kern_ms = [a.elapsed_time(b) for a, b in zip(ks, ke)]
+    return step_ms, kern_ms, clk.summary()
+
+
+def run_multi_genome(args, world, rank, local):
+    """4 references (5, 12, 25, 50 Mbp) and 16,000,000 queries of U[20,250] bp
+    in one multi-reference call (count only); the launch shape is autotuned."""
+    import torch
+
+    import paper_1303_3692_gb300.sa as sa
+    from paper_1303_3692_gb300 import autotune, datagen
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    refs, qb, qo, qref, _ = datagen.multi_genome(scale=args.scale)
+    t0 = time.perf_counter()
+    idxs = [sa.sa_build(torch.from_numpy(r).to(dev)) for r in refs]
+    build_s = time.perf_counter() - t0
+    n_q = qo.size - 1
+    qb_d, qo_d, qr_d = (torch.from_numpy(x).to(dev) for x in (qb, qo, qref))
+    params, tune = autotune.autotune(idxs, qb_d, qo_d, q_ref=qr_d, use_cache=False)
+    step_ms, kern_ms, clocks = _time_count_steps(idxs, qb_d, qo_d, qr_d, params, args, local)
     total_s = sum(step_ms) / 1e3
     value = args.steps * n_q / total_s
     if rank != 0:
@@ -202,7 +222,42 @@ def run_multi_genome(args, world, rank, local):
                    "kmer_k": [i.kmer_k for i in idxs], "l2": "flushed between steps"},
         "query_bases_per_s": value * (float(qo[-1]) / n_q),
         "search_kernel_ms": statistics.mean(kern_ms), "step_ms_all": step_ms, "build_s": build_s,
-        "gpu_launches": args.steps * 2, "clocks": clk.summary(),
+        "gpu_launches": args.steps * 3, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_plain_small(args, world, rank, local):
+    """1 Mbp iid reference, 100,000 queries of 32 bp (half copied from the
+    reference, half random), count only.  The whole index fits in L2, so the
+    number is latency- and launch-bound; L2 is still flushed between steps."""
+    import torch
+
+    import paper_1303_3692_gb300.sa as sa
+    from paper_1303_3692_gb300 import datagen
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = datagen.plain_small()
+    t0 = time.perf_counter()
+    idx = sa.sa_build(torch.from_numpy(w.ref).to(dev))
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    n_q = w.q_offsets.size - 1
+    qb_d, qo_d = torch.from_numpy(w.q_bases).to(dev), torch.from_numpy(w.q_offsets).to(dev)
+    step_ms, kern_ms, clocks = _time_count_steps(idx, qb_d, qo_d, None, sa.sa_search_params(), args, local)
+    total_s = sum(step_ms) / 1e3
+    value = args.steps * n_q / total_s
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "plain-1Mbp-100k-q32", "n": int(w.ref.size), "queries_per_step": n_q, "m": 32,
+                   "mode": "count", "kmer_k": idx.kmer_k, "l2": "flushed between steps; index L2-resident size"},
+        "query_bases_per_s": value * 32, "search_kernel_ms": statistics.mean(kern_ms), "step_ms_all": step_ms,
+        "build_s": build_s, "gpu_launches": args.steps * 3, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
 
@@ -480,8 +535,8 @@ def run_ours(args, world, rank, local):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     kern_ms = [s.elapsed_time(e) for s, e in zip(k_starts, k_ends)]
     phases = {
-        "pack_queries_kernel": statistics.mean(a.elapsed_time(b) for a, b in zip(starts, k_starts)),
-        "search_kernel": statistics.mean(kern_ms),
+        "pack_batch_kernel": statistics.mean(a.elapsed_time(b) for a, b in zip(starts, k_starts)),
+        "search": statistics.mean(kern_ms),
         "locate": statistics.mean(a.elapsed_time(b) for a, b in zip(mids, ends)),
     }
     total_s = sum(step_ms) / 1e3
@@ -515,7 +570,8 @@ def run_ours(args, world, rank, local):
     h2d = int(qb_h.numel() + qo_h.numel() * 8)
     d2h = int(res_h.numel() * 8 + offs_h.numel() * 8 + total_pos * 4)
 
-    # The plain one-thread-per-query kernel (Alg. 1) on the same batch.
+    # The plain one-thread-per-query kernel (Alg. 1) on the same batch (the
+    # call packs the batch first, like the product path).
     plain_ms = []
     for _ in range(2):
         flush.zero_()
@@ -565,10 +621,11 @@ def run_ours(args, world, rank, local):
         "datagen_s": gen_s,
         "positions_per_step": total_pos,
         "plain_kernel": {"ms": statistics.mean(plain_ms), "queries_per_s": n_q / (statistics.mean(plain_ms) / 1e3),
-                         "search_speedup": statistics.mean(plain_ms) / statistics.mean(kern_ms)},
+                         "search_speedup": statistics.mean(plain_ms) / (phases["pack_batch_kernel"] +
+                                                                        phases["search"])},
         "e2e": {"value": n_q / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_s * 1e3},
-        "gpu_launches": args.steps * 5,
+        "gpu_launches": args.steps * 6,
         "roofline": roof,
         "cpu_baseline": cpu,
         "clocks": clocks,
@@ -611,10 +668,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=6.0)
-    ap.add_argument("--workload", choices=["repetitive-100m", "multi-genome", "serving", "human-sized"],
+    ap.add_argument("--workload", choices=["repetitive-100m", "plain-small", "multi-genome", "serving",
+                                           "human-sized"],
                     default="repetitive-100m")
-    ap.add_argument("--human-queries", type=int, default=22_000_000,
-                    help="queries of the 3.1 Gbp workload (the recipe's full batch is 110,000,000)")
+    ap.add_argument("--human-queries", type=int, default=110_000_000,
+                    help="queries per step of the 3.1 Gbp workload (100M sampled + 10M random)")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--pool", type=int, default=300_000, help="queries pre-generated per reference (serving)")
     args = ap.parse_args()
@@ -623,6 +681,8 @@ def main():
         run_reference(args, world, rank)
     elif args.workload == "multi-genome":
         run_multi_genome(args, world, rank, local)
+    elif args.workload == "plain-small":
+        run_plain_small(args, world, rank, local)
     elif args.workload == "serving":
         run_serving(args, world, rank, local)
     elif args.workload == "human-sized":

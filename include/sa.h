@@ -83,7 +83,9 @@ typedef struct sa_search_params {
     void *search_events[2];     /* optional cudaEvent_t pair, recorded on the stream right
                                    before and after the search kernel (kernel timing) */
     uint32_t flags;             /* SA_PARAM_Q_RANGE: q_first and q_total are given */
-    uint32_t reserved0;
+    uint32_t front_probes;      /* probes per query in the one-thread-per-query first
+                                   pass before a query joins the worklist of the
+                                   persistent kernel (0: 3; at most 64) */
     uint64_t q_first;           /* q_offsets[0] */
     uint64_t q_total;           /* q_offsets[n_q] - q_offsets[0] */
     uint32_t reserved[4];
@@ -104,13 +106,17 @@ typedef struct sa_search_params {
  * the search reads:
  *  - the key table kept in shared memory (first 64 bases of the suffixes at
  *    ranks floor((2p+1) n / 2^(l+1)), the top levels of the binary search);
- *  - one 16-byte record per rank (the first 48 bases of that suffix and its
- *    position), so that a probe reads one aligned record;
- *  - unless SA_NO_KMER, the k-mer table kmer[x] = number of suffixes that
- *    sort before the k-base string x, for all 4^k strings (+1 entry = n);
- *    a query of m >= k bases whose first k bases are x lies strictly between
- *    ranks kmer[x] - 1 and kmer[x + 1].  Automatic k: the largest k with
- *    4^k <= 4n, in 1..15 (4^k * 4 bytes: 1 GB at k = 14 for 10^8 bases).
+ *  - one 32-byte record per rank (the first 112 bases of that suffix and its
+ *    position), so that a probe reads one aligned sector;
+ *  - unless SA_NO_KMER, the k-mer table: for each of the 4^k k-base
+ *    strings x a 64-byte entry with lo = kmer[x] = number of suffixes that
+ *    sort before x and hi = kmer[x + 1] (a query of m >= k bases whose first
+ *    k bases are x lies strictly between ranks lo - 1 and hi), and the
+ *    position and first 192 bases of the suffix at rank
+ *    lo - 1 + (hi - lo + 1) / 2, the first pivot of the binary search over
+ *    that bracket -- so one read brackets a query and makes its first probe.
+ *    Automatic k: the largest k with 4^k <= 3n, in 1..15 (64 * 4^k bytes:
+ *    17 GB at k = 14 for 10^8 bases, 69 GB at k = 15).
  * Device memory: about n/4 + (width + 32) n bytes + the k-mer table.
  *
  *  text   n bytes of bases, host or device memory.
@@ -142,6 +148,15 @@ int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_inde
  *  n_q        number of queries, < 2^32 (0 is allowed and does nothing).
  *  out        n_q results (host or device).
  *  stream     CUDA stream or NULL.
+ *
+ * The work runs as three kernels on the stream: the batch's bases are packed
+ * 2 bits each beside a per-base validity mask; a one-thread-per-query pass
+ * brackets each query of m >= k bases by the k-mer table and probes it up to
+ * sa_search_params.front_probes times; a persistent kernel finishes the
+ * queries that remain (and every query of an index without a k-mer table or
+ * shorter than k).  Scratch device memory from the library pool: about
+ * 12 * ceil(total / 32) + 64 n_q bytes (total = the batch's bases), plus the
+ * staging copies of host inputs.
  *
  * A query that cannot be searched -- a byte outside {A,C,G,T,a,c,g,t}, an
  * out-of-range q_ref, or offsets inconsistent with the batch's range -- gets
@@ -243,8 +258,9 @@ int sa_load(const char *path, void *stream, sa_index **out);
 int sa_index_info(const sa_index *idx, uint64_t *n, uint32_t *width, uint32_t *key_depth,
                   uint32_t *kmer_k, uint64_t *device_bytes);
 
-/* Copies the k-mer table (4^k + 1 uint32) to dst (host or device).
- * SA_ERR_ARG if the index has none. */
+/* Copies the k-mer table's counts kmer[x] (4^k + 1 uint32, the last = n) to
+ * dst (host or device; a host copy synchronizes the stream).  SA_ERR_ARG if
+ * the index has none. */
 int sa_copy_kmer_table(const sa_index *idx, void *dst, void *stream);
 
 /* Copies the suffix array (n elements of the index's width) to dst (host or

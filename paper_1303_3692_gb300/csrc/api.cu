@@ -131,6 +131,7 @@ uint32_t floor_log2(uint64_t x) {
 }
 
 constexpr uint32_t kDefaultDepth = 13;
+constexpr uint32_t kDefaultFrontProbes = 3;
 constexpr uint32_t kSmemBudget = 200 * 1024;
 
 int check_refs(const sa_index *const *refs, uint32_t n_refs, uint32_t *width) {
@@ -171,7 +172,7 @@ uint32_t fill_ref_table(const sa_index *const *refs, uint32_t n_refs, uint32_t w
         d.keys = x->keys;
         d.keylen = x->keylen;
         d.rec = x->rec;
-        d.kmer = x->kmer;
+        d.krt = x->krt;
         d.kmer_k = x->kmer_k;
         d.n = x->n;
         d.depth = x->depth;
@@ -230,15 +231,15 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     const uint32_t *ref_d = n_refs > 1 || q_ref ? device_view(q_ref, n_q, sc, &err) : nullptr;
     const bool out_dev = on_device(out);
     sa_result *out_d = out_dev ? out : sc.get<sa_result>(n_q);
-    const uint64_t nslots = (total >> 7) + n_q + 1;
-    if (nslots >= (1ull << 32)) return SA_ERR_ARG;
-    uint64_t *qwords = sc.get<uint64_t>(4 * nslots);
-    uint4 *meta = sc.get<uint4>(2 * n_q);
-    if (((uintptr_t)meta & 31u) != 0) return SA_ERR_CUDA;  // the search reads 32-byte records
-    int *flags = sc.get<int>(4);  // [0] pack error, [1] status
+    const uint64_t nwords = (total + 31) / 32;
+    uint64_t *tq = sc.get<uint64_t>(nwords + SA_TQ_PAD_WORDS);
+    uint32_t *tv = sc.get<uint32_t>(nwords + SA_TQ_PAD_WORDS);
+    uint4 *wrec = plain ? nullptr : sc.get<uint4>(4 * n_q);
+    int *flags = sc.get<int>(4);  // [0] pack error, [1] status, [2] worklist count
     unsigned long long *counter = sc.get<unsigned long long>(1);
     if (sc.failed) return SA_ERR_NOMEM;
     if (err != cudaSuccess) return status_from_cuda(err);
+    if (((uintptr_t)wrec & 31u) != 0) return SA_ERR_CUDA;  // the search reads 32-byte records
     if ((err = cudaMemsetAsync(flags, 0, 4 * sizeof(int), s)) != cudaSuccess) return status_from_cuda(err);
     if ((err = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s)) != cudaSuccess)
         return status_from_cuda(err);
@@ -256,13 +257,16 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     L.n_refs = n_refs;
     L.width = width;
     L.ascii = bases_d;
-    L.qwords = qwords;
+    L.tq = tq;
+    L.tv = tv;
+    L.nwords = nwords;
     L.q_off = off_d;
     L.first = first;
     L.total = total;
     L.q_ref = ref_d;
     L.n_q = n_q;
-    L.meta = meta;
+    L.wrec = wrec;
+    L.wl_count = reinterpret_cast<uint32_t *>(flags + 2);
     L.out = out_d;
     L.pack_err = flags;
     L.counter = counter;
@@ -271,12 +275,19 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     L.threads = threads;
     L.blocks = (uint32_t)sms * bps;
     L.chunk = params && params->chunk ? params->chunk : 64;
+    L.front_probes = params && params->front_probes ? params->front_probes : kDefaultFrontProbes;
+    if (L.front_probes > 64) return SA_ERR_ARG;
 
-    if ((err = launch_pack_queries(L, flags, s)) != cudaSuccess) return status_from_cuda(err);
+    if ((err = launch_pack_batch(L, tq, tv, s)) != cudaSuccess) return status_from_cuda(err);
     cudaEvent_t ev0 = params ? reinterpret_cast<cudaEvent_t>(params->search_events[0]) : nullptr;
     cudaEvent_t ev1 = params ? reinterpret_cast<cudaEvent_t>(params->search_events[1]) : nullptr;
     if (ev0 && (err = cudaEventRecord(ev0, s)) != cudaSuccess) return status_from_cuda(err);
-    err = plain ? launch_search_plain(L, s) : launch_search(L, s);
+    if (plain) {
+        err = launch_search_plain(L, s);
+    } else {
+        err = launch_front(L, s);
+        if (err == cudaSuccess) err = launch_search(L, s);
+    }
     if (err != cudaSuccess) return status_from_cuda(err);
     if (ev1 && (err = cudaEventRecord(ev1, s)) != cudaSuccess) return status_from_cuda(err);
     if (!out_dev) {
@@ -301,24 +312,25 @@ void free_index(sa_index *idx) {
     if (idx->keys) cudaFree(idx->keys);
     if (idx->keylen) cudaFree(idx->keylen);
     if (idx->rec) cudaFree(idx->rec);
-    if (idx->kmer) cudaFree(idx->kmer);
+    if (idx->krt) cudaFree(idx->krt);
     delete idx;
 }
 
 uint32_t table_entries(uint32_t depth) { return depth >= 4 ? (1u << depth) : 16u; }
 
-// Automatic k: the largest k with 4^k <= 4n, in 1..15 (one suffix per two to
-// eight k-mers; the table is at most 16n bytes, half the records' size).
+// Automatic k: the largest k with 4^k <= 3n, in 1..15 (at least one k-mer
+// entry per three suffixes on average, so that most brackets hold one or
+// two suffixes; the table takes at most 192 bytes per base).
 uint32_t auto_kmer_k(uint64_t n) {
     uint32_t k = 1;
-    while (k < 15 && (1ull << (2 * (k + 1))) <= 4 * n) k++;
+    while (k < 15 && (1ull << (2 * (k + 1))) <= 3 * n) k++;
     return k;
 }
 
 // Allocates the device arrays of an index whose n, width, depth and kmer_k
-// are set: first the text, suffix array and key table; the records and the
-// k-mer table (about 32n bytes) are allocated separately, after the build's
-// scratch has been returned, so the two never coexist.
+// are set: first the text, suffix array and key table; the records (32n
+// bytes) and the k-mer table (64 * 4^k bytes) are allocated separately,
+// after the build's scratch has been returned, so the two never coexist.
 int alloc_index(sa_index *idx) {
     idx->nwords = (idx->n + 31) / 32;
     const size_t tb = (idx->nwords + SA_PAD_WORDS) * sizeof(uint64_t);
@@ -342,8 +354,8 @@ int alloc_search_arrays(sa_index *idx) {
     }
     size_t mb = 0;
     if (idx->kmer_k) {
-        mb = ((1ull << (2 * idx->kmer_k)) + 1) * sizeof(uint32_t);
-        if (cudaMalloc(&idx->kmer, mb) != cudaSuccess) {
+        mb = (1ull << (2 * idx->kmer_k)) * 4 * sizeof(uint4);
+        if (cudaMalloc(&idx->krt, mb) != cudaSuccess) {
             cudaGetLastError();
             return SA_ERR_NOMEM;
         }
@@ -436,6 +448,7 @@ int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_inde
         if (err == cudaSuccess) err = launch_build_records(idx, s);
         if (err == cudaSuccess) err = launch_build_kmer(idx, s);
         if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+        cudaMemPoolTrimTo(scratch_pool(idx->device), 0);
         st = status_from_cuda(err);
     }
     if (st) {
@@ -638,6 +651,7 @@ int sa_load(const char *path, void *stream, sa_index **out) {
     if (e == cudaSuccess) e = launch_build_records(idx, s);
     if (e == cudaSuccess) e = launch_build_kmer(idx, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaMemPoolTrimTo(scratch_pool(idx->device), 0);
     if (e != cudaSuccess) {
         free_index(idx);
         return status_from_cuda(e);
@@ -658,10 +672,18 @@ int sa_index_info(const sa_index *idx, uint64_t *n, uint32_t *width, uint32_t *k
 }
 
 int sa_copy_kmer_table(const sa_index *idx, void *dst, void *stream) {
-    if (!idx || !dst || !idx->kmer) return SA_ERR_ARG;
+    if (!idx || !dst || !idx->krt) return SA_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const size_t bytes = ((1ull << (2 * idx->kmer_k)) + 1) * sizeof(uint32_t);
-    return status_from_cuda(cudaMemcpyAsync(dst, idx->kmer, bytes, cudaMemcpyDefault, s));
+    if (on_device(dst)) return status_from_cuda(launch_copy_kmer_counts(idx, static_cast<uint32_t *>(dst), s));
+    uint32_t *tmp = nullptr;
+    cudaError_t e = scratch_alloc(reinterpret_cast<void **>(&tmp), bytes, s);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    e = launch_copy_kmer_counts(idx, tmp, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, tmp, bytes, cudaMemcpyDeviceToHost, s);
+    scratch_free(tmp, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return status_from_cuda(e);
 }
 
 int sa_copy_suffix_array(const sa_index *idx, void *dst, void *stream) {

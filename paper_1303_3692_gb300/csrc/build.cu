@@ -286,9 +286,70 @@ __global__ void build_kmer_kernel(const uint4 *__restrict__ rec, uint64_t n, uin
     }
 }
 
+// k-mer table entry, 64 bytes (4 uint4) per k-base string x:
+//   {lo, hi, pos, clamp}: ranks [lo, hi) hold the suffixes that sort at or
+//     after x and before x + 1 (those with prefix x, and any suffix shorter
+//     than k that falls between the two), lo = number of suffixes sorting
+//     before x; when hi > lo, pos is the position of the suffix at rank
+//     M = lo - 1 + (hi - lo + 1) / 2 -- the first pivot of the lockstep binary
+//     search over (lo - 1, hi) -- and clamp = min(192, n - pos) the number of
+//     its first 192 bases that exist;
+//   three uint4: the first 192 bases of that suffix as six packed words.
+// One aligned 64-byte read therefore brackets a query of m >= k bases and
+// makes its first probe.
+__global__ void build_krt_kernel(const uint32_t *__restrict__ kmer, const uint4 *__restrict__ rec,
+                                 const uint64_t *__restrict__ T, uint64_t n, uint32_t k, uint4 *__restrict__ krt) {
+    const uint64_t entries = 1ull << (2 * k);
+    GS_LOOP(x, entries) {
+        const uint32_t lo = kmer[x], hi = kmer[x + 1];
+        uint4 h = make_uint4(lo, hi, 0u, 0u);
+        uint64_t e[6] = {0, 0, 0, 0, 0, 0};
+        if (hi > lo) {
+            const uint32_t M = lo + (hi - lo + 1u) / 2u - 1u;
+            const uint64_t pos = rec[2 * (uint64_t)M + 1].w;
+            const uint64_t left = n - pos;  // >= 1
+            h.z = (uint32_t)pos;
+            h.w = (uint32_t)(left < 192 ? left : 192);
+#pragma unroll
+            for (int j = 0; j < 6; j++) {
+                const uint64_t b = pos + 32ull * j;
+                e[j] = b < n ? text_window(T, b) : 0ull;
+            }
+        }
+        uint4 *dst = krt + 4 * x;
+        dst[0] = h;
+        dst[1] = make_uint4((uint32_t)e[0], (uint32_t)(e[0] >> 32), (uint32_t)e[1], (uint32_t)(e[1] >> 32));
+        dst[2] = make_uint4((uint32_t)e[2], (uint32_t)(e[2] >> 32), (uint32_t)e[3], (uint32_t)(e[3] >> 32));
+        dst[3] = make_uint4((uint32_t)e[4], (uint32_t)(e[4] >> 32), (uint32_t)e[5], (uint32_t)(e[5] >> 32));
+    }
+}
+
+// The plain counts kmer[x] = lo of every entry, and kmer[4^k] = n.
+__global__ void krt_lo_kernel(const uint4 *__restrict__ krt, uint64_t n, uint32_t k, uint32_t *__restrict__ out) {
+    const uint64_t entries = 1ull << (2 * k);
+    GS_LOOP(x, entries + 1) out[x] = x < entries ? krt[4 * x].x : (uint32_t)n;
+}
+
 cudaError_t launch_build_kmer(sa_index *idx, cudaStream_t s) {
-    if (!idx->kmer) return cudaSuccess;
-    build_kmer_kernel<<<grid_for(idx->n + 1), kThreads, 0, s>>>(idx->rec, idx->n, idx->kmer_k, idx->kmer);
+    if (!idx->krt) return cudaSuccess;
+    const uint64_t entries = 1ull << (2 * idx->kmer_k);
+    uint32_t *kmer = nullptr;
+    cudaError_t e = scratch_alloc(reinterpret_cast<void **>(&kmer), (entries + 1) * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    build_kmer_kernel<<<grid_for(idx->n + 1), kThreads, 0, s>>>(idx->rec, idx->n, idx->kmer_k, kmer);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        build_krt_kernel<<<grid_for(entries), kThreads, 0, s>>>(kmer, idx->rec, idx->text, idx->n, idx->kmer_k,
+                                                                idx->krt);
+        e = cudaGetLastError();
+    }
+    scratch_free(kmer, s);
+    return e;
+}
+
+cudaError_t launch_copy_kmer_counts(const sa_index *idx, uint32_t *dst, cudaStream_t s) {
+    const uint64_t entries = 1ull << (2 * idx->kmer_k);
+    krt_lo_kernel<<<grid_for(entries + 1), kThreads, 0, s>>>(idx->krt, idx->n, idx->kmer_k, dst);
     return cudaGetLastError();
 }
 

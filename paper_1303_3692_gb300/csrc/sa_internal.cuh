@@ -8,11 +8,12 @@
 //   and every packed text carries SA_PAD_WORDS zero words after its last
 //   word, so a 32-base window starting at any base < n reads in bounds.
 //
-// Packed queries: query q occupies 32-byte slots starting at slot
-// ((q_offsets[q] - q_offsets[0]) >> 7) + q of the query word buffer (4 words
-// per slot).  For consecutive queries the start grows by at least
-// ceil(m_q / 128) slots, so no scan is needed to place them, and a query's
-// first 128 bases sit in one aligned 32-byte sector.
+// Packed query batch: the bases of a whole batch (q_offsets[0] ..
+// q_offsets[n_q]) packed like a text, 32 per word, with SA_TQ_PAD_WORDS zero
+// words after the last, and one 32-bit mask per word whose bit i marks base
+// 32 w + i as not in {A,C,G,T,a,c,g,t}.  Query q's bases start at base
+// q_offsets[q] - q_offsets[0], so any of its 32-base windows is one
+// text_window read.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -20,6 +21,7 @@
 #include "../../include/sa.h"
 
 #define SA_PAD_WORDS 2
+#define SA_TQ_PAD_WORDS 6
 #define SA_MAX_REFS 64
 #define SA_MAX_KEY_DEPTH 14
 
@@ -32,7 +34,7 @@ struct RefDesc {
     const uint4 *keys;      // 2^depth key entries: 64 bases as two words (x,y = w0; z,w = w1)
     const uint8_t *keylen;  // 2^depth clamp lengths min(64, n - SA[rank])
     const uint4 *rec;       // 2n uint4: n 32-byte suffix records, see sa_index::rec
-    const uint32_t *kmer;   // 4^kmer_k + 1 entries, see sa_index::kmer (null: none)
+    const uint4 *krt;       // 4^kmer_k 64-byte k-mer entries, see sa_index::krt (null: none)
     uint64_t n;
     uint32_t depth;         // key-table depth d of this index; K = 2^d - 1 samples
     uint32_t smem_off;      // byte offset of this table in the search kernel's shared memory
@@ -101,14 +103,8 @@ __device__ __forceinline__ uint32_t base_code(uint32_t c) {
     return ok ? code : 4u;
 }
 
-// First 32-byte slot of a query whose bases start at byte a_rel of the batch.
-__host__ __device__ __forceinline__ uint64_t query_slot(uint64_t a_rel, uint64_t q) { return (a_rel >> 7) + q; }
-
-// Per-query record written by the pack kernel for the search, 32 bytes (two
-// uint4): x, y = the starting bracket (L, R) of the binary search
-// (L = 0xFFFFFFFF for -1), z = m (kQueryInvalid for a query that cannot be
-// searched), w = its first slot; then the query's first two packed words
-// (bases 0-63), so that the search starts from one sector.
+// Marks a query that cannot be searched (a byte that is not a base,
+// inconsistent offsets or an out-of-range reference id).
 constexpr uint32_t kQueryInvalid = 0xFFFFFFFFu;
 
 // Four ASCII bytes (little-endian in v) to four 2-bit codes in the low byte,
@@ -192,6 +188,103 @@ __device__ __forceinline__ uint64_t sa_at(const void *sa, uint64_t i) {
     return (uint64_t)__ldg(reinterpret_cast<const IdxT *>(sa) + i);
 }
 
+// Predicated read-only loads: when pred is false nothing is read and the
+// outputs keep their values.  p must be 32-byte (ldg32_if) or 16-byte
+// (ldg16_if) aligned when pred is true.
+__device__ __forceinline__ void ldg32_if(bool pred, const void *p, uint4 *lo, uint4 *hi) {
+    unsigned long long a = 0, b = 0, c = 0, d = 0;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %5, 0;\n\t"
+        "@p ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];\n\t}"
+        : "+l"(a), "+l"(b), "+l"(c), "+l"(d)
+        : "l"(p), "r"((uint32_t)pred));
+    *lo = make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
+    *hi = make_uint4((uint32_t)c, (uint32_t)(c >> 32), (uint32_t)d, (uint32_t)(d >> 32));
+}
+
+__device__ __forceinline__ void ldg16_if(bool pred, const void *p, uint64_t *x, uint64_t *y) {
+    unsigned long long a = 0, b = 0;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %3, 0;\n\t"
+        "@p ld.global.nc.v2.u64 {%0, %1}, [%2];\n\t}"
+        : "+l"(a), "+l"(b)
+        : "l"(p), "r"((uint32_t)pred));
+    *x = a;
+    *y = b;
+}
+
+__device__ __forceinline__ uint32_t ldg_u32_or(bool pred, const uint32_t *p, uint32_t v) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t"
+        "@p ld.global.nc.u32 %0, [%1];\n\t}"
+        : "+r"(v)
+        : "l"(p), "r"((uint32_t)pred));
+    return v;
+}
+
+// One window of a compare: q and t hold qlen and tlen bases (tlen may be 0)
+// aligned at the top bits, starting at base `off` of the query; bits past
+// qlen or tlen are ignored.  Returns 2 when the window does not decide, else
+// the outcome with *lcp set.
+__device__ __forceinline__ int cmp_window(uint64_t q, uint64_t t, uint32_t qlen, uint32_t tlen, uint32_t off,
+                                          uint32_t m, uint32_t *lcp) {
+    const uint64_t x = q ^ t;
+    const uint32_t d = x ? ((uint32_t)__clzll((long long)x) >> 1) : 32u;
+    if (d < min(qlen, tlen)) {
+        *lcp = off + d;
+        return q < t ? CMP_LESS : CMP_GREATER;
+    }
+    if (tlen < qlen) {
+        *lcp = off + tlen;
+        return CMP_GREATER;
+    }
+    if (off + qlen >= m) {
+        *lcp = m;
+        return CMP_PREFIX;
+    }
+    return 2;
+}
+
+// P (bases 0-63 in q0, q1, bases 64-127 in x2, x3; length m >= 1) against a
+// 32-byte suffix record (r0 = bases 0-63, r1 = bases 64-95, 96-111 and the
+// position).  Sets *undecided when all 112 bases agree, m > 112 and the
+// suffix has 112 bases or more; the compare then continues in the text.
+__device__ __forceinline__ int cmp_record(uint64_t q0, uint64_t q1, uint64_t x2, uint64_t x3, uint32_t m, uint4 r0,
+                                          uint4 r1, uint32_t n, uint32_t *lcp, bool *undecided) {
+    const uint32_t klen = min(112u, n - r1.w);
+    int c = cmp_window(q0, ((uint64_t)r0.y << 32) | r0.x, min(32u, m), min(32u, klen), 0u, m, lcp);
+    if (c != 2) return c;
+    c = cmp_window(q1, ((uint64_t)r0.w << 32) | r0.z, min(32u, m - 32u), min(32u, klen - 32u), 32u, m, lcp);
+    if (c != 2) return c;
+    c = cmp_window(x2, ((uint64_t)r1.y << 32) | r1.x, min(32u, m - 64u), min(32u, klen - 64u), 64u, m, lcp);
+    if (c != 2) return c;
+    c = cmp_window(x3 & 0xFFFFFFFF00000000ull, (uint64_t)r1.z << 32, min(16u, m - 96u), min(16u, klen - 96u), 96u,
+                   m, lcp);
+    if (c != 2) return c;
+    *undecided = true;
+    *lcp = 112;
+    return CMP_PREFIX;
+}
+
+// Query P (length m >= 1, bases at base qa of the packed batch tq) against
+// the suffix at p of a text of n < 2^32 bases, from the 32-aligned base below
+// `start` (< m; all bases before it are known equal).
+__device__ __forceinline__ int cmp_suffix_tq(const uint64_t *__restrict__ T, uint32_t n, uint32_t p,
+                                             const uint64_t *__restrict__ tq, uint64_t qa, uint32_t m,
+                                             uint32_t start, uint32_t *lcp) {
+    uint32_t off = start & ~31u;
+    const uint32_t rem = n - p;
+    for (;;) {
+        const uint32_t qlen = min(32u, m - off);
+        const uint32_t tlen = off < rem ? min(32u, rem - off) : 0u;
+        const uint64_t q = text_window(tq, qa + off);
+        const uint64_t t = tlen ? text_window(T, (uint64_t)(p + off)) : 0ull;
+        const int c = cmp_window(q, t, qlen, tlen, off, m, lcp);
+        if (c != 2) return c;
+        off += 32u;
+    }
+}
+
 }  // namespace sa
 
 // ---------------------------------------------------------------------------
@@ -212,8 +305,13 @@ struct sa_index {
                          // (bases 0-95) and the 16 bases 96-111 in the high-to-low bits of a
                          // 32-bit word, then SA[i]: {w0.lo, w0.hi, w1.lo, w1.hi}, {w2.lo,
                          // w2.hi, w3, SA[i]}
-    uint32_t *kmer;      // device, 4^kmer_k + 1 entries: kmer[x] = number of suffixes that
-                         // sort before the k-base string x (x as a 2k-bit number); null if none
+    uint4 *krt;          // device, 4^kmer_k k-mer entries of 64 bytes (4 uint4) for the k-base
+                         // strings x (x as a 2k-bit number): {lo, hi, pos, clamp} -- the ranks
+                         // [lo, hi) of the suffixes sorting at or after x and before x + 1,
+                         // lo = number of suffixes that sort before x, and the position of the
+                         // suffix at the first pivot lo - 1 + (hi - lo + 1) / 2 with clamp =
+                         // min(192, n - pos) -- then the first 192 bases of that suffix as six
+                         // packed words; null if none
     uint32_t kmer_k;
     uint64_t device_bytes;
 };
@@ -229,12 +327,11 @@ int device_sm_count();
 // Kernels launched from the API translation unit.
 cudaError_t launch_pack_text(const char *ascii, uint64_t n, uint64_t *words, uint64_t nwords_padded,
                              int *err_flag, cudaStream_t s);
-struct SearchLaunch;
-cudaError_t launch_pack_queries(const SearchLaunch &L, int *err_flag, cudaStream_t s);
 int build_suffix_array(sa_index *idx, cudaStream_t s);
 cudaError_t launch_build_keys(sa_index *idx, cudaStream_t s);
 cudaError_t launch_build_records(sa_index *idx, cudaStream_t s);
 cudaError_t launch_build_kmer(sa_index *idx, cudaStream_t s);
+cudaError_t launch_copy_kmer_counts(const sa_index *idx, uint32_t *dst, cudaStream_t s);
 
 // Descriptors of every index a call uses, passed by value as a kernel
 // parameter (64 x 72 bytes; kernel parameters may take up to 32 KB).
@@ -247,20 +344,31 @@ struct SearchLaunch {
     uint32_t n_refs;
     uint32_t width;
     const char *ascii;        // query bases, indexed by q_off[q] - first
-    uint64_t *qwords;         // packed queries (written by the pack kernel)
+    const uint64_t *tq;       // packed batch: nwords + SA_TQ_PAD_WORDS words
+    const uint32_t *tv;       // per packed word: bit i set = base 32 w + i is not a base
+    uint64_t nwords;          // ceil(total / 32)
     const uint64_t *q_off;    // n_q + 1 offsets
     uint64_t first;           // q_off[0]
     uint64_t total;           // q_off[n_q] - q_off[0]: query ranges past it are invalid
     const uint32_t *q_ref;    // null when n_refs == 1
     uint64_t n_q;
-    uint4 *meta;              // 2 n_q uint4: per-query records written by the pack kernel
+    uint4 *wrec;              // worklist records, 64 bytes (4 uint4) each, n_q of room
+    uint32_t *wl_count;       // device: records in the worklist
     sa_result *out;
     int *pack_err;            // device flag: some query had a non-ACGT byte or bad offsets
     unsigned long long *counter;
     int *status;
     uint32_t smem_bytes;      // shared-memory key tables
     uint32_t threads, blocks, chunk;
+    uint32_t front_probes;    // probes per query in the first pass
 };
+// Worklist record of a query the first pass did not finish (64 bytes):
+//   {L, R, m, q}            a bracket (L, R) holding both bounds (L = -1 is
+//                           0xFFFFFFFF), the length and the query's index
+//   {ref, 0, qa.lo, qa.hi}  its reference and first base in the packed batch
+//   {w0, w1}, {w2, w3}      its first 128 bases (packed words)
+cudaError_t launch_pack_batch(const SearchLaunch &L, uint64_t *tq, uint32_t *tv, cudaStream_t s);
+cudaError_t launch_front(const SearchLaunch &L, cudaStream_t s);
 cudaError_t launch_search(const SearchLaunch &L, cudaStream_t s);
 cudaError_t launch_search_plain(const SearchLaunch &L, cudaStream_t s);
 uint32_t search_table_bytes(uint32_t depth);  // shared-memory bytes of a depth-d key table

@@ -1,8 +1,9 @@
 // search.cu -- the suffix-array interval of every query (Section IV).
 //
-// Two kernels compute the same [lo, hi):
-//
-// search_kernel (the product path).  Persistent CTAs, one query per lane.
+// search_kernel (second pass of the product path).  Persistent CTAs, one
+//   query of the first pass's worklist per lane (the queries front_kernel
+//   did not finish: wide brackets, queries shorter than k, indexes without a
+//   k-mer table).
 //   * Each CTA first copies every index's sampled-key table into shared
 //     memory with bulk asynchronous copies (cp.async.bulk, completion on an
 //     mbarrier with a bounded wait).  The table holds the first 64 bases of
@@ -35,7 +36,7 @@ struct SmemDesc {
     const uint64_t *text;
     const void *sa;
     const uint4 *rec;
-    const uint32_t *kmer;
+    const uint4 *krt;
     uint64_t n;
     uint32_t off;
     uint32_t depth;
@@ -145,98 +146,27 @@ __device__ __forceinline__ void write_result(sa_result *out, uint64_t q, uint64_
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s for the key-table copy
 
-// 32-bit form of cmp_query_suffix for texts of n < 2^32 bases: the suffix at
-// p has n - p >= 1 bases; the compare starts at the 32-aligned base below
-// `start` (< m).
-__device__ __forceinline__ int cmp_suffix32(const uint64_t *__restrict__ T, uint32_t n, uint32_t p,
-                                            const uint64_t *__restrict__ Q, uint32_t m, uint32_t start,
-                                            uint32_t *lcp) {
-    uint32_t off = start & ~31u;
-    const uint32_t rem = n - p;
-    for (;;) {
-        const uint32_t qlen = min(32u, m - off);
-        const uint32_t tlen = off < rem ? min(32u, rem - off) : 0u;
-        const uint64_t q = __ldg(Q + (off >> 5));
-        const uint64_t t = tlen ? text_window(T, (uint64_t)(p + off)) : 0ull;
-        const uint64_t x = q ^ t;
-        const uint32_t d = x ? ((uint32_t)__clzll((long long)x) >> 1) : 32u;
-        if (d < min(qlen, tlen)) {
-            *lcp = off + d;
-            return q < t ? CMP_LESS : CMP_GREATER;
-        }
-        if (tlen < qlen) {
-            *lcp = off + tlen;
-            return CMP_GREATER;
-        }
-        if (off + 32u >= m) {
-            *lcp = m;
-            return CMP_PREFIX;
-        }
-        off += 32u;
-    }
-}
-
-// One window of a compare: q and t hold qlen and tlen bases (tlen may be 0)
-// aligned at the top bits, starting at base `off` of the query.  Returns 2
-// when the window does not decide, else the outcome with *lcp set.
-__device__ __forceinline__ int cmp_window(uint64_t q, uint64_t t, uint32_t qlen, uint32_t tlen, uint32_t off,
-                                          uint32_t m, uint32_t *lcp) {
-    const uint64_t x = q ^ t;
-    const uint32_t d = x ? ((uint32_t)__clzll((long long)x) >> 1) : 32u;
-    if (d < min(qlen, tlen)) {
-        *lcp = off + d;
-        return q < t ? CMP_LESS : CMP_GREATER;
-    }
-    if (tlen < qlen) {
-        *lcp = off + tlen;
-        return CMP_GREATER;
-    }
-    if (off + qlen >= m) {
-        *lcp = m;
-        return CMP_PREFIX;
-    }
-    return 2;
-}
-
-// P (first 64 bases q0, q1, then Q; length m) against a 32-byte suffix record
-// (r0 = bases 0-63, r1 = bases 64-95, 96-111 and the position).  Sets
-// *undecided when all 112 bases agree, m > 112 and the suffix has 112 bases
-// or more; the compare then continues in the text.
-__device__ __forceinline__ int cmp_record(uint64_t q0, uint64_t q1, const uint64_t *__restrict__ Q, uint32_t m,
-                                          uint4 r0, uint4 r1, uint32_t n, uint32_t *lcp, bool *undecided) {
-    const uint32_t klen = min(112u, n - r1.w);
-    int c = cmp_window(q0, ((uint64_t)r0.y << 32) | r0.x, min(32u, m), min(32u, klen), 0u, m, lcp);
-    if (c != 2) return c;
-    c = cmp_window(q1, ((uint64_t)r0.w << 32) | r0.z, min(32u, m - 32u), min(32u, klen - 32u), 32u, m, lcp);
-    if (c != 2) return c;
-    c = cmp_window(__ldg(Q + 2), ((uint64_t)r1.y << 32) | r1.x, min(32u, m - 64u), min(32u, klen - 64u), 64u, m,
-                   lcp);
-    if (c != 2) return c;
-    c = cmp_window(__ldg(Q + 3) & 0xFFFFFFFF00000000ull, (uint64_t)r1.z << 32, min(16u, m - 96u),
-                   min(16u, klen - 96u), 96u, m, lcp);
-    if (c != 2) return c;
-    *undecided = true;
-    *lcp = 112;
-    return CMP_PREFIX;
-}
-
-// The search of one query is a sequence of steps, one compare each, run by
-// its lane one step per loop iteration so that the 32 lanes of a warp stay in
-// the same short code path:
-//   init      read the query's 32-byte record from the pack kernel (length,
-//             slot, starting bracket and the first 64 bases); when the index
-//             has a k-mer table and m >= k the bracket comes from the table
-//             entries of its first k bases and the descent is skipped;
+// The search of one query is a sequence of steps, one per loop iteration of
+// its lane, and every step that touches device memory issues one round of
+// independent loads, so that the 32 lanes of a warp wait for one round per
+// iteration (a lane starting a query never holds up the lanes that probe):
+//   init      read the query's 64-byte worklist record (bracket, length,
+//             index, reference, first base in the packed batch, first 64
+//             bases); a query with a k-mer bracket probes from it, any other
+//             descends the key table first;
 //   descent   compare with the key of level-order node k in shared memory
 //             (k = 0 once the table's depth is passed or the bounds split);
 //   deep      load the suffix record of rank M = L + (R - L)/2 (32 bytes: 112
-//             bases and SA[M]) and compare; only when all 112 bases tie does
-//             the compare continue in the packed text.
+//             bases and SA[M]) -- with query bases 64-127 from the worklist
+//             record in the same round -- and compare; only when all 112
+//             bases tie does the compare continue in the packed text.
 // Ranks are 32-bit modular: L = 0xFFFFFFFF stands for -1, and since every
 // rank is in [-1, n] with n < 2^32 - 1, R - L and L + (R - L)/2 are exact.
 // phase 0: both bounds share (L, R); a prefix match splits them into the
 // lower bound in (L, M] (phase 1) and the upper bound in [M, R), kept in
 // (HL, HR) until phase 1 ends (phase 2).
+// Warps take chunks of worklist entries from one global counter, each
+// chunk's base fetched while the previous chunk is handed out.
 // Launch-bound variants: kOcc = 1 (1024 threads, <= 64 registers), 3 (512
 // threads x 3 CTAs, <= 40 registers), 8 (256 threads x 8 CTAs, <= 32 registers).
 template <int kOcc>
@@ -261,10 +191,12 @@ __global__ void __launch_bounds__(Occ<kOcc>::threads, Occ<kOcc>::blocks)
     __shared__ SmemDesc sdesc[SA_MAX_REFS];
     __shared__ __align__(8) uint64_t mbar;
     const unsigned tid = threadIdx.x;
+    const uint32_t n_work = __ldg(a.wl_count);
+    if (n_work == 0) return;
 
     for (unsigned r = tid; r < a.n_refs; r += blockDim.x) {
         const RefDesc &d = a.refs.r[r];
-        sdesc[r] = SmemDesc{d.text, d.sa, d.rec, d.kmer, d.n, d.smem_off, d.use_depth, d.kmer_k};
+        sdesc[r] = SmemDesc{d.text, d.sa, d.rec, d.krt, d.n, d.smem_off, d.use_depth, d.kmer_k};
     }
     if (tid == 0) {
         mbar_init(&mbar, 1);
@@ -300,18 +232,19 @@ __global__ void __launch_bounds__(Occ<kOcc>::threads, Occ<kOcc>::blocks)
     const uint64_t *T = d0.text;
     const void *SAp = d0.sa;
     const uint4 *REC = d0.rec;
-    const uint32_t *KM = d0.kmer;
+    const uint4 *KM = d0.krt;
     uint32_t kk = d0.kmer_k;
     uint32_t n = (uint32_t)d0.n;
     const uint8_t *Ktab = smem + d0.off;
     uint32_t depth = d0.depth;
 
-    uint64_t pool_next = 0, pool_end = 0;  // warp-uniform chunk of query ids
+    uint64_t pool_next = 0, pool_end = 0;  // warp-uniform chunk of worklist entries
+    unsigned long long pre = 0;             // lane 0: base of the next chunk
+    if (lane == 0) pre = atomicAdd(a.counter, (unsigned long long)a.chunk);
     bool exhausted = false;
     bool active = false, fresh = false;
-    uint32_t q = 0, m = 0;
-    const uint64_t *Q = nullptr;
-    uint64_t q0 = 0, q1 = 0;
+    uint32_t wi = 0, qout = 0, m = 0;
+    uint64_t qa = 0, q0 = 0, q1 = 0;
     uint32_t L = 0, R = 0, HL = 0, HR = 0, lcpL = 0, lcpR = 0, hlcpL = 0, hlcpR = 0, lo = 0;
     uint32_t k = 0, phase = 0;
 
@@ -319,21 +252,20 @@ __global__ void __launch_bounds__(Occ<kOcc>::threads, Occ<kOcc>::blocks)
         unsigned need = __ballot_sync(0xFFFFFFFFu, !active);
         while (need != 0u && !exhausted) {
             if (pool_next >= pool_end) {
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(a.counter, (unsigned long long)a.chunk);
-                base = __shfl_sync(0xFFFFFFFFu, base, 0);
-                if (base >= a.n_q) {
+                const unsigned long long base = __shfl_sync(0xFFFFFFFFu, pre, 0);
+                if (base >= n_work) {
                     exhausted = true;
                     break;
                 }
                 pool_next = base;
-                pool_end = min((uint64_t)base + a.chunk, a.n_q);
+                pool_end = min((uint64_t)base + a.chunk, (uint64_t)n_work);
+                if (lane == 0) pre = atomicAdd(a.counter, (unsigned long long)a.chunk);
             }
             const uint64_t left = pool_end - pool_next;
             const uint32_t avail = left < 32ull ? (uint32_t)left : 32u;
             const uint32_t rank = __popc(need & lanemask_lt);
             if (((need >> lane) & 1u) && rank < avail) {
-                q = (uint32_t)(pool_next + rank);
+                wi = (uint32_t)(pool_next + rank);
                 active = true;
                 fresh = true;
             }
@@ -343,54 +275,46 @@ __global__ void __launch_bounds__(Occ<kOcc>::threads, Occ<kOcc>::blocks)
         if (__ballot_sync(0xFFFFFFFFu, active) == 0u) break;
         if (!active) continue;
 
-        if (fresh) {
+        // This iteration's one round of loads: the worklist record (init) or
+        // the suffix record at the pivot and query bases 64-127 (deep).
+        const bool init = fresh;
+        const bool deep = !init && k == 0;
+        uint32_t M = L + ((R - L) >> 1);
+        const uint4 *wrec = a.wrec + 4 * (size_t)wi;
+        uint4 r0, r1;
+        ldg32_if(init || deep, init ? (const void *)wrec : (const void *)(REC + 2 * (size_t)M), &r0, &r1);
+        uint64_t x2 = 0, x3 = 0;
+        ldg16_if(init || (deep && m > 64u), wrec + (init ? 2 : 3), &x2, &x3);
+
+        if (init) {
             fresh = false;
-            uint4 mt, mw;
-            ldg32(a.meta + 2 * (size_t)q, &mt, &mw);
-            const uint32_t r = (!kSingle && a.q_ref) ? __ldg(a.q_ref + q) : 0u;
-            if (mt.z == kQueryInvalid || r >= a.n_refs) {
-                write_result(a.out, q, ~0ull, ~0ull);
-                active = false;
-                continue;
-            }
+            qout = r0.w;
+            const uint32_t r = r1.x;
             if (!kSingle) {
-                const SmemDesc d = sdesc[r];
+                const SmemDesc d = sdesc[r < a.n_refs ? r : 0u];
                 T = d.text;
                 SAp = d.sa;
                 REC = d.rec;
-                KM = d.kmer;
+                KM = d.krt;
                 kk = d.kmer_k;
                 n = (uint32_t)d.n;
                 Ktab = smem + d.off;
                 depth = d.depth;
             }
-            m = mt.z;
-            if (m == 0) {
-                write_result(a.out, q, 0, n);
-                active = false;
-                continue;
-            }
-            Q = a.qwords + 4 * (size_t)mt.w;
-            q0 = ((uint64_t)mw.y << 32) | mw.x;
-            q1 = ((uint64_t)mw.w << 32) | mw.z;
+            m = r0.z;
+            qa = ((uint64_t)r1.w << 32) | r1.z;
+            q0 = x2;
+            q1 = x3;
             lcpL = lcpR = 0;
             phase = 0;
-            L = mt.x;  // the pack kernel's bracket: the k-mer table's, or [-1, n)
-            R = mt.y;
-            if (KM != nullptr && m >= kk) {
-                k = 0;
-                if (R - L <= 1u) {
-                    write_result(a.out, q, R, R);
-                    active = false;
-                    continue;
-                }
-            } else {
-                k = depth ? 1u : 0u;
-            }
+            L = r0.x;
+            R = r0.y;
+            k = (KM != nullptr && m >= kk) ? 0u : (depth ? 1u : 0u);
+            continue;
         }
 
         int c;
-        uint32_t l, M;
+        uint32_t l;
         if (k != 0) {
             // Descent: node k at level lvl samples rank floor((2p+1) n / 2^(lvl+1)).
             const uint32_t lvl = 31u - __clz(k);
@@ -400,16 +324,13 @@ __global__ void __launch_bounds__(Occ<kOcc>::threads, Occ<kOcc>::blocks)
             const uint32_t klen = Ktab[(16u << depth) + k];
             bool und = false;
             c = cmp_key(q0, q1, m, kv, klen, &l, &und);
-            if (und) c = cmp_suffix32(T, n, (uint32_t)sa_at<IdxT>(SAp, M), Q, m, 64u, &l);
+            if (und) c = cmp_suffix_tq(T, n, (uint32_t)sa_at<IdxT>(SAp, M), a.tq, qa, m, 64u, &l);
             const uint32_t nk = 2u * k + (c == CMP_GREATER ? 1u : 0u);
             k = (c == CMP_PREFIX || nk >= (1u << depth)) ? 0u : nk;
         } else {
-            M = L + ((R - L) >> 1);
-            uint4 r0, r1;
-            ldg32(REC + 2 * (size_t)M, &r0, &r1);
             bool und = false;
-            c = cmp_record(q0, q1, Q, m, r0, r1, n, &l, &und);
-            if (und) c = cmp_suffix32(T, n, r1.w, Q, m, max(112u, min(lcpL, lcpR)), &l);
+            c = cmp_record(q0, q1, x2, x3, m, r0, r1, n, &l, &und);
+            if (und) c = cmp_suffix_tq(T, n, r1.w, a.tq, qa, m, max(112u, min(lcpL, lcpR)), &l);
         }
         if (c == CMP_PREFIX && phase == 0) {
             HL = M;
@@ -440,21 +361,23 @@ __global__ void __launch_bounds__(Occ<kOcc>::threads, Occ<kOcc>::blocks)
             }
             if (R - L <= 1u) {
                 const uint32_t lo_out = phase == 0 ? R : lo;
-                write_result(a.out, q, lo_out, R);
+                write_result(a.out, qout, lo_out, R);
                 active = false;
             }
         }
     }
 }
 
-// Alg. 1: compare the query with the m-prefix of S_p one base at a time.
+// Alg. 1: compare the query (bases qa.. of the packed batch) with the
+// m-prefix of S_p one base at a time.
 __device__ __forceinline__ int cmp_plain(const uint64_t *__restrict__ T, uint64_t n, uint64_t p,
-                                         const uint64_t *__restrict__ Q, uint32_t m) {
+                                         const uint64_t *__restrict__ tq, uint64_t qa, uint32_t m) {
     for (uint32_t k = 0; k < m; k++) {
         if (p + k >= n) return CMP_GREATER;
         const uint64_t b = p + k;
         const uint32_t tb = (uint32_t)(__ldg(T + (b >> 5)) >> (62u - 2u * (uint32_t)(b & 31u))) & 3u;
-        const uint32_t qb = (uint32_t)(__ldg(Q + (k >> 5)) >> (62u - 2u * (k & 31u))) & 3u;
+        const uint64_t c = qa + k;
+        const uint32_t qb = (uint32_t)(__ldg(tq + (c >> 5)) >> (62u - 2u * (uint32_t)(c & 31u))) & 3u;
         if (tb != qb) return qb < tb ? CMP_LESS : CMP_GREATER;
     }
     return CMP_PREFIX;
@@ -467,13 +390,18 @@ __global__ void __launch_bounds__(256) search_plain_kernel(const __grid_constant
     const uint64_t a0 = __ldg(a.q_off + q) - a.first;
     const uint64_t a1 = __ldg(a.q_off + q + 1) - a.first;
     const uint32_t r = a.q_ref ? __ldg(a.q_ref + q) : 0u;
-    const bool bad = a.meta[2 * q].z == kQueryInvalid;
-    if (bad || r >= a.n_refs || a1 < a0 || a1 > a.total || a1 - a0 >= (1ull << 31)) {
+    const bool range_ok = a0 <= a1 && a1 <= a.total && a1 - a0 < (1ull << 31);
+    bool bad = !range_ok;
+    if (range_ok) {  // every base of the query must be one of A, C, G, T
+        for (uint64_t b = a0; b < a1; b++)
+            if ((__ldg(a.tv + (b >> 5)) >> (b & 31u)) & 1u) bad = true;
+    }
+    if (bad || r >= a.n_refs) {
+        if (bad) atomicOr(a.pack_err, 1);
         write_result(a.out, q, ~0ull, ~0ull);
         return;
     }
     const uint32_t m = (uint32_t)(a1 - a0);
-    const uint64_t *Q = a.qwords + 4 * query_slot(a0, q);
     const RefDesc &d = a.refs.r[r];
     const uint64_t *T = d.text;
     const uint64_t n = d.n;
@@ -481,7 +409,7 @@ __global__ void __launch_bounds__(256) search_plain_kernel(const __grid_constant
     int64_t L = -1, R = (int64_t)n;
     while (R > L + 1) {
         const int64_t pivot = (L + R) >> 1;
-        if (cmp_plain(T, n, sa_at<IdxT>(d.sa, (uint64_t)pivot), Q, m) <= 0)
+        if (cmp_plain(T, n, sa_at<IdxT>(d.sa, (uint64_t)pivot), a.tq, a0, m) <= 0)
             R = pivot;
         else
             L = pivot;
@@ -492,7 +420,7 @@ __global__ void __launch_bounds__(256) search_plain_kernel(const __grid_constant
     R = (int64_t)n;
     while (R > L + 1) {
         const int64_t pivot = (L + R) >> 1;
-        if (cmp_plain(T, n, sa_at<IdxT>(d.sa, (uint64_t)pivot), Q, m) < 0)
+        if (cmp_plain(T, n, sa_at<IdxT>(d.sa, (uint64_t)pivot), a.tq, a0, m) < 0)
             R = pivot;
         else
             L = pivot;

@@ -54,7 +54,7 @@ class sa_result(ctypes.Structure):
 
 class sa_search_params(ctypes.Structure):
     _fields_ = [("threads_per_block", _u32), ("blocks_per_sm", _u32), ("key_depth", _u32), ("chunk", _u32),
-                ("search_events", _vp * 2), ("flags", _u32), ("reserved0", _u32), ("q_first", _u64),
+                ("search_events", _vp * 2), ("flags", _u32), ("front_probes", _u32), ("q_first", _u64),
                 ("q_total", _u64), ("reserved", _u32 * 4)]
 
 

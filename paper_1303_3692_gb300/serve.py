@@ -48,9 +48,12 @@ class Request:
 
 
 def scratch_bytes(n_q: int, n_bases: int) -> int:
-    """Device scratch one search call takes from the library's pool: packed
-    query slots, 32-byte per-query records and small flags."""
-    return 32 * ((n_bases >> 7) + n_q + 1) + 32 * n_q + 64
+    """Device scratch one search call takes from the library's pool: the
+    packed batch (8 bytes per 32 bases) and its validity masks (4 bytes per 32
+    bases), 64 bytes of worklist room per query, small flags, and 256 bytes of
+    alignment per allocation."""
+    words = (n_bases + 31) // 32 + 6
+    return 12 * words + 64 * n_q + 64 + 5 * 256
 
 
 def form_batch(queue: List[Request], max_q: int, max_bases: int, budget: int):
