@@ -16,8 +16,8 @@
 //     in all.
 // A query still undecided after that (a bracket wider than the probes could
 // resolve, a query shorter than k, an index without a k-mer table) is
-// appended to a worklist -- a 64-byte record holding a bracket of both
-// bounds, its length, index, reference, first base and first 128 bases --
+// appended to a worklist -- a 32-byte record holding a bracket of both
+// bounds, its length, index, reference and first base in the packed batch --
 // which the persistent kernel of search.cu then finishes.
 #include "sa_internal.cuh"
 
@@ -70,6 +70,7 @@ __device__ __forceinline__ int cmp_entry(const uint64_t w[4], uint32_t m, const 
 template <bool kSingle>
 __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_constant__ SearchLaunch a) {
     __shared__ FrontDesc sdesc[SA_MAX_REFS];
+    __shared__ uint4 s_stage[kFrontThreads / 32][32][2];  // worklist records staged per warp
     for (unsigned r = threadIdx.x; r < a.n_refs; r += blockDim.x) {
         const RefDesc &d = a.refs.r[r];
         sdesc[r] = FrontDesc{d.text, d.rec, d.krt, (uint32_t)d.n, d.kmer_k};
@@ -77,7 +78,22 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
     __syncthreads();
 
     const unsigned lane = threadIdx.x & 31u;
+    const unsigned wib = threadIdx.x >> 5;
     const unsigned lanemask_lt = (1u << lane) - 1u;
+    uint32_t staged = 0;  // warp-uniform: records in s_stage[wib]
+    // Moves the warp's staged records to the worklist (one atomic).
+    auto flush = [&](uint32_t cnt) {
+        if (cnt == 0u) return;
+        uint32_t at = 0;
+        if (lane == 0) at = atomicAdd(a.wl_count, cnt);
+        at = __shfl_sync(0xFFFFFFFFu, at, 0);
+        if (lane < cnt) {
+            uint4 *dst = a.wrec + 2 * (size_t)(at + lane);
+            dst[0] = s_stage[wib][lane][0];
+            dst[1] = s_stage[wib][lane][1];
+        }
+        __syncwarp();
+    };
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t warp_first = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
     const uint64_t *__restrict__ tq = a.tq;
@@ -220,25 +236,27 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
 
         // The rest goes to the worklist with one bracket of both bounds:
         // phase 0 (L, R); phase 1 (L, HR) (lo in (L, M], hi in [M, HR));
-        // phase 2 (lo - 1, R) (lo known, hi in (L, R) with L >= lo).
+        // phase 2 (lo - 1, R) (lo known, hi in (L, R) with L >= lo).  Records
+        // are staged per warp in shared memory and flushed 32 at a time, so
+        // the global count takes one atomic per 32 records.
         const bool rest = live && !done;
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, rest);
         if (bal != 0u) {
-            uint32_t at = 0;
-            if (lane == 0) at = atomicAdd(a.wl_count, (uint32_t)__popc(bal));
-            at = __shfl_sync(0xFFFFFFFFu, at, 0);
-            if (rest) {
-                const uint32_t i = at + __popc(bal & lanemask_lt);
-                const uint32_t bl = phase == 2 ? lo - 1u : L;
-                const uint32_t br = phase == 1 ? HR : R;
-                uint4 *rec = a.wrec + 4 * (size_t)i;
-                rec[0] = make_uint4(bl, br, m, (uint32_t)q);
-                rec[1] = make_uint4(r, 0u, (uint32_t)qa, (uint32_t)(qa >> 32));
-                rec[2] = make_uint4((uint32_t)w[0], (uint32_t)(w[0] >> 32), (uint32_t)w[1], (uint32_t)(w[1] >> 32));
-                rec[3] = make_uint4((uint32_t)w[2], (uint32_t)(w[2] >> 32), (uint32_t)w[3], (uint32_t)(w[3] >> 32));
+            const uint32_t n_new = (uint32_t)__popc(bal);
+            if (staged + n_new > 32u) {
+                flush(staged);
+                staged = 0;
             }
+            if (rest) {
+                const uint32_t slot = staged + __popc(bal & lanemask_lt);
+                s_stage[wib][slot][0] = make_uint4(phase == 2 ? lo - 1u : L, phase == 1 ? HR : R, m, (uint32_t)q);
+                s_stage[wib][slot][1] = make_uint4(r, 0u, (uint32_t)qa, (uint32_t)(qa >> 32));
+            }
+            staged += n_new;
+            __syncwarp();
         }
     }
+    flush(staged);
     if (__any_sync(0xFFFFFFFFu, any_bad) && lane == 0) atomicOr(a.pack_err, 1);
 }
 
