@@ -245,7 +245,8 @@ def run_plain_small(args, world, rank, local):
     build_s = time.perf_counter() - t0
     n_q = w.q_offsets.size - 1
     qb_d, qo_d = torch.from_numpy(w.q_bases).to(dev), torch.from_numpy(w.q_offsets).to(dev)
-    step_ms, kern_ms, clocks = _time_count_steps(idx, qb_d, qo_d, None, sa.sa_search_params(), args, local)
+    step_ms, kern_ms, clocks = _time_count_steps(idx, qb_d, qo_d, None,
+                                                 sa.sa_search_params(front_probes=args.front_probes), args, local)
     total_s = sum(step_ms) / 1e3
     value = args.steps * n_q / total_s
     if rank != 0:
@@ -294,7 +295,7 @@ def run_human_sized(args, world, rank, local):
         e.record(stream)
         return e
 
-    p = sa.sa_search_params()
+    p = sa.sa_search_params(front_probes=args.front_probes)
     p.flags = sa.SA_PARAM_Q_RANGE
     p.q_first, p.q_total = 0, int(w.q_offsets[-1])
     offs = torch.empty(n_q + 1, dtype=torch.int64, device=dev)
@@ -484,7 +485,7 @@ def run_ours(args, world, rank, local):
         return e
 
     ev_s = [lib_event() for _ in range(2)]
-    params = sa.sa_search_params()
+    params = sa.sa_search_params(front_probes=args.front_probes)
     params.search_events[0] = ev_s[0].cuda_event
     params.search_events[1] = ev_s[1].cuda_event
     # the batch's offsets range is known on the host: the call never synchronizes
@@ -674,6 +675,8 @@ def main():
     ap.add_argument("--human-queries", type=int, default=110_000_000,
                     help="queries per step of the 3.1 Gbp workload (100M sampled + 10M random)")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--front-probes", type=int, default=0,
+                    help="probes per query in the first search pass (0: the library's default)")
     ap.add_argument("--pool", type=int, default=300_000, help="queries pre-generated per reference (serving)")
     args = ap.parse_args()
     world, rank, local = dist_env()
