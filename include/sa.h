@@ -210,6 +210,21 @@ int sa_locate(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_re
               const sa_result *res, uint64_t n_q, uint32_t cap, uint64_t *out_offsets,
               void *out_pos, uint64_t out_pos_capacity, void *stream);
 
+/*
+ * sa_search_locate -- sa_search_batch_ex followed by sa_locate on the same
+ * stream in one call, with the same arguments and results as the two calls.
+ *
+ *  refs ... params  as for sa_search_batch_ex (out: n_q results).
+ *  cap ... out_pos_capacity  as for sa_locate.
+ *
+ * Errors: as sa_search_batch (an invalid query gets the all-ones result and
+ * no positions; the other queries are located) and sa_locate.
+ */
+int sa_search_locate(const sa_index *const *refs, uint32_t n_refs, const char *q_bases,
+                     const uint64_t *q_offsets, const uint32_t *q_ref, uint64_t n_q,
+                     sa_result *out, uint32_t cap, uint64_t *out_offsets, void *out_pos,
+                     uint64_t out_pos_capacity, void *stream, const sa_search_params *params);
+
 /* Largest n_q that sa_locate_noalloc accepts (its static scratch holds one
  * 8-byte partial sum per 4096 queries, plus one: 131,080 bytes). */
 #define SA_LOCATE_NOALLOC_MAX_QUERIES (1ull << 26)

@@ -476,9 +476,11 @@ int sa_search_batch_plain(const sa_index *const *refs, uint32_t n_refs, const ch
     return search_impl(refs, n_refs, q_bases, q_offsets, q_ref, n_q, out, stream, nullptr, true);
 }
 
-int sa_locate(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_ref, const sa_result *res,
-              uint64_t n_q, uint32_t cap, uint64_t *out_offsets, void *out_pos, uint64_t out_pos_capacity,
-              void *stream) {
+namespace sa {
+
+int locate_impl(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_ref, const sa_result *res,
+                uint64_t n_q, uint32_t cap, uint64_t *out_offsets, void *out_pos, uint64_t out_pos_capacity,
+                void *stream) {
     uint32_t width = 0;
     int st = check_refs(refs, n_refs, &width);
     if (st) return st;
@@ -527,6 +529,26 @@ int sa_locate(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_re
         if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return status_from_cuda(err);
     }
     return SA_OK;
+}
+
+}  // namespace sa
+
+int sa_locate(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_ref, const sa_result *res,
+              uint64_t n_q, uint32_t cap, uint64_t *out_offsets, void *out_pos, uint64_t out_pos_capacity,
+              void *stream) {
+    return sa::locate_impl(refs, n_refs, q_ref, res, n_q, cap, out_offsets, out_pos, out_pos_capacity, stream);
+}
+
+int sa_search_locate(const sa_index *const *refs, uint32_t n_refs, const char *q_bases, const uint64_t *q_offsets,
+                     const uint32_t *q_ref, uint64_t n_q, sa_result *out, uint32_t cap, uint64_t *out_offsets,
+                     void *out_pos, uint64_t out_pos_capacity, void *stream, const sa_search_params *params) {
+    using namespace sa;
+    if (!out_offsets || (n_q && !out)) return SA_ERR_ARG;
+    const int st = search_impl(refs, n_refs, q_bases, q_offsets, q_ref, n_q, out, stream, params, false);
+    if (st && st != SA_ERR_BASE && st != SA_ERR_ARG) return st;
+    // invalid queries carry the all-ones result (no positions); the rest are located
+    const int lst = locate_impl(refs, n_refs, q_ref, out, n_q, cap, out_offsets, out_pos, out_pos_capacity, stream);
+    return lst ? lst : st;
 }
 
 // sa_locate without allocation: device buffers only, scan scratch in the

@@ -66,6 +66,8 @@ SIGNATURES = {
                                           ctypes.POINTER(sa_search_params)]),
     "sa_search_batch_plain": (ctypes.c_int, [ctypes.POINTER(_vp), _u32, _vp, _vp, _vp, _u64, _vp, _vp]),
     "sa_locate": (ctypes.c_int, [ctypes.POINTER(_vp), _u32, _vp, _vp, _u64, _u32, _vp, _vp, _u64, _vp]),
+    "sa_search_locate": (ctypes.c_int, [ctypes.POINTER(_vp), _u32, _vp, _vp, _vp, _u64, _vp, _u32, _vp, _vp, _u64,
+                                        _vp, ctypes.POINTER(sa_search_params)]),
     "sa_locate_noalloc": (ctypes.c_int, [ctypes.POINTER(_vp), _u32, _vp, _vp, _u64, _u32, _vp, _vp, _u64, _vp]),
     "sa_save": (ctypes.c_int, [_vp, ctypes.c_char_p, _vp]),
     "sa_load": (ctypes.c_int, [ctypes.c_char_p, _vp, ctypes.POINTER(_vp)]),
@@ -278,3 +280,28 @@ def sa_locate(refs, res, cap: int, q_ref=None, out_offsets=None, out_pos=None, c
     _check(lib().sa_locate(arr, nr, _ptr(q_ref), _ptr(res), n_q, cap, _ptr(out_offsets), _ptr(out_pos), capacity, s),
            "sa_locate")
     return out_offsets, out_pos
+
+
+def sa_search_locate(refs, q_bases, q_offsets, cap: int, q_ref=None, out=None, out_offsets=None, out_pos=None,
+                     capacity=None, stream=None, params=None):
+    """sa_search_batch then sa_locate in one call: (results, offsets, positions).
+    The caller gives out_pos (and capacity) or gets positions for at most
+    `capacity` (default: cap * n_q) matches on the offsets' device."""
+    arr, nr = _refs(refs)
+    n_q = int((q_offsets.numel() if isinstance(q_offsets, torch.Tensor) else len(q_offsets)) - 1)
+    if out is None:
+        out = _out_like(n_q, q_offsets)
+    dev = out.device if isinstance(out, torch.Tensor) else "cpu"
+    dt = torch.int32 if (refs if isinstance(refs, Index) else refs[0]).width == 4 else torch.int64
+    if out_offsets is None:
+        out_offsets = torch.empty(n_q + 1, dtype=torch.int64, device=dev)
+    if out_pos is None:
+        capacity = cap * n_q if capacity is None else capacity
+        out_pos = torch.empty(max(capacity, 1), dtype=dt, device=dev)
+    if capacity is None:
+        capacity = int(out_pos.numel() if isinstance(out_pos, torch.Tensor) else out_pos.size)
+    p = params if params is not None else sa_search_params()
+    _check(lib().sa_search_locate(arr, nr, _ptr(q_bases), _ptr(q_offsets), _ptr(q_ref), n_q, _ptr(out), cap,
+                                  _ptr(out_offsets), _ptr(out_pos), capacity, _stream(stream), ctypes.byref(p)),
+           "sa_search_locate")
+    return out, out_offsets, out_pos

@@ -51,6 +51,11 @@ def test_search_and_locate_full_size(c2):
     starts = np.repeat(lo, k)
     within = np.arange(int(k.sum())) - np.repeat(offs[:-1], k)
     assert np.array_equal(pos.cpu().numpy().astype(np.int64), osa[starts + within])
+    # the one-call path that the benchmark times gives the same results and positions
+    res2, offs2, pos2 = sa.sa_search_locate(idx, qb, qo, w.cap)
+    assert torch.equal(res2, res)
+    assert np.array_equal(offs2.cpu().numpy(), offs)
+    assert torch.equal(pos2[:int(offs[-1])].cpu(), pos[:int(offs[-1])].cpu())
     # every exact copy from the reference occurs; counts agree with brute force on a sample
     rng = np.random.default_rng(3)
     for q in rng.choice(np.nonzero(w.sampled)[0], 8, replace=False):

@@ -322,3 +322,49 @@ def test_q_range_param_sub_batch(sa):
     p.q_total = int(sub[-1] - sub[0]) - 5
     c = sa.sa_search_batch(idx, qb_d, sub_d, params=p).cpu()
     assert (c[-1] == -1).all() and torch.equal(c[:-1], a[:-1])
+
+
+def _check_positions(res, offs, pos, lo, hi, osa, cap):
+    """Offsets are the prefix sum of min(count, cap); query q's positions are
+    SA[lo_q], SA[lo_q + 1], ... (suffix-array order)."""
+    k = np.minimum(hi - lo, cap)
+    assert offs[0] == 0 and np.array_equal(np.diff(offs), k)
+    starts = np.repeat(lo, k)
+    within = np.arange(int(k.sum())) - np.repeat(offs[:-1], k)
+    assert np.array_equal(pos[:int(k.sum())].astype(np.int64), osa[starts + within])
+
+
+@pytest.mark.parametrize("cap", [1, 16])
+def test_search_locate_one_call(sa, cap):
+    """sa_search_locate: the search hands each query's SA[lo] to the locate;
+    results and positions equal the oracle's, for queries shorter and longer
+    than k and repeats with many copies."""
+    ref = datagen.reference(300_000, 81, sd_cover=0.1, tandem_cover=0.05)
+    T = oracle.normalize(ref)
+    osa = oracle.sa_naive(T)
+    idx = sa.sa_build(_dev(ref))
+    qb, qo, _ = datagen.queries(ref, 20000, 82, m=(1, 160), frac_sampled=0.8, subs=(0, 1))
+    res, offs, pos = sa.sa_search_locate(idx, _dev(qb), _dev(qo), cap)
+    lo, hi = oracle.search_batch(T, osa, qb, qo, threads=oracle.cpu_threads())
+    got = res.cpu().numpy()
+    assert np.array_equal(got[:, 0], lo) and np.array_equal(got[:, 1], hi) and np.array_equal(got[:, 2], hi - lo)
+    _check_positions(got, offs.cpu().numpy(), pos.cpu().numpy(), lo, hi, osa, cap)
+
+
+def test_search_locate_multi_reference(sa):
+    refs, qb, qo, qref, _ = datagen.multi_genome(scale=0.002)
+    idxs = [sa.sa_build(_dev(r)) for r in refs]
+    res, offs, pos = sa.sa_search_locate(idxs, _dev(qb), _dev(qo), 8, q_ref=_dev(qref))
+    got = res.cpu().numpy()
+    offs = offs.cpu().numpy()
+    pos = pos.cpu().numpy().astype(np.int64)
+    k = np.minimum(got[:, 2], 8)
+    assert offs[0] == 0 and np.array_equal(np.diff(offs), k)
+    for r, ref in enumerate(refs):
+        T = oracle.normalize(ref)
+        osa = oracle.sa_naive(T)
+        for q in np.nonzero(qref == r)[0][:400]:
+            P = qb[qo[q]:qo[q + 1]]
+            lo, hi = oracle.search(T, osa, P)
+            assert (got[q, 0], got[q, 1]) == (lo, hi), q
+            assert np.array_equal(pos[offs[q]:offs[q + 1]], osa[lo:lo + min(hi - lo, 8)]), q
