@@ -595,6 +595,15 @@ def run_ours(args, world, rank, local):
             "frac": per_kernel[dominant]["frac"], "traffic": traffic, "kernel": dominant,
             "peak_kind": peak_kind, "bytes_per_query": KERNEL_BYTES_PER_QUERY[dominant],
             "bytes_source": BYTES_SOURCE, "per_kernel": per_kernel}
+    # The search's probes are dependent random reads: their ceiling is the
+    # device's random-read rate (DRAM row activations), measured here over a
+    # 4 GB buffer with the same resident threads per SM as the first pass.
+    rr_peak = sa.sa_random_read_rate(4 << 30, 1024, 64)
+    rr_ach = RANDOM_ACCESSES_PER_QUERY["search"] * n_q / (phases["search"] / 1e3)
+    roof["random_reads"] = {"kernel": "search", "achieved": rr_ach / 1e9, "peak": rr_peak / 1e9,
+                            "unit": "G reads/s", "frac": rr_ach / rr_peak,
+                            "reads_per_query": RANDOM_ACCESSES_PER_QUERY["search"],
+                            "peak_source": "sa_random_read_rate(4 GB, 1024 threads/SM, 64 dependent reads)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

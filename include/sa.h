@@ -273,6 +273,20 @@ int sa_load(const char *path, void *stream, sa_index **out);
 int sa_index_info(const sa_index *idx, uint64_t *n, uint32_t *width, uint32_t *key_depth,
                   uint32_t *kmer_k, uint64_t *device_bytes);
 
+/*
+ * sa_random_read_rate -- measures the device's rate of dependent random
+ * 32-byte reads, the ceiling of the search's probes: threads_per_sm threads
+ * per SM each follow a chain of `steps` reads, each read's address derived
+ * from the value of the one before, over a buffer of buffer_bytes (allocated
+ * and freed by the call; make it far larger than L2).  *reads_per_s receives
+ * the reads completed per second.  Synchronous.
+ *
+ * Errors: SA_ERR_ARG (buffer_bytes < 4096, steps == 0, threads_per_sm not a
+ * multiple of 32 in 32..2048), SA_ERR_NOMEM, SA_ERR_CUDA.
+ */
+int sa_random_read_rate(uint64_t buffer_bytes, uint32_t threads_per_sm, uint32_t steps, double *reads_per_s,
+                        void *stream);
+
 /* Copies the k-mer table's counts kmer[x] (4^k + 1 uint32, the last = n) to
  * dst (host or device; a host copy synchronizes the stream).  SA_ERR_ARG if
  * the index has none. */

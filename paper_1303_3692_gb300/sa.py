@@ -78,6 +78,7 @@ SIGNATURES = {
     "sa_free": (None, [_vp]),
     "sa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sa_version": (_u32, []),
+    "sa_random_read_rate": (ctypes.c_int, [_u64, _u32, _u32, ctypes.POINTER(ctypes.c_double), _vp]),
 }
 
 _lib = None
@@ -305,3 +306,12 @@ def sa_search_locate(refs, q_bases, q_offsets, cap: int, q_ref=None, out=None, o
                                   _ptr(out_offsets), _ptr(out_pos), capacity, _stream(stream), ctypes.byref(p)),
            "sa_search_locate")
     return out, out_offsets, out_pos
+
+
+def sa_random_read_rate(buffer_bytes: int = 4 << 30, threads_per_sm: int = 1024, steps: int = 64,
+                        stream=None) -> float:
+    """Dependent random 32-byte reads per second over a buffer far larger than L2."""
+    r = ctypes.c_double(0.0)
+    _check(lib().sa_random_read_rate(buffer_bytes, threads_per_sm, steps, ctypes.byref(r), _stream(stream)),
+           "sa_random_read_rate")
+    return r.value

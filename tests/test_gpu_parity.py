@@ -368,3 +368,12 @@ def test_search_locate_multi_reference(sa):
             lo, hi = oracle.search(T, osa, P)
             assert (got[q, 0], got[q, 1]) == (lo, hi), q
             assert np.array_equal(pos[offs[q]:offs[q + 1]], osa[lo:lo + min(hi - lo, 8)]), q
+
+
+def test_random_read_rate_probe(sa):
+    """The device's dependent random-read rate (the bench's ceiling for the
+    search's probes) is measurable and its arguments are checked."""
+    r = sa.sa_random_read_rate(64 << 20, 256, 8)
+    assert 1e8 < r < 1e13
+    with pytest.raises(sa.SAError):
+        sa.sa_random_read_rate(64 << 20, 33, 8)
