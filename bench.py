@@ -59,10 +59,11 @@ KERNEL_BYTES_PER_QUERY = {
 RANDOM_ACCESSES_PER_QUERY = {"search": 1.41265}
 BYTES_SOURCE = "oracle/bytes_model.py --workload repetitive-100m (k = 14)"
 
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# DRAM bytes (read + write) per step of the dominant phase from one ncu
 # capture (--set full, 100 Mbp workload), valid only while the kernel sources
 # hash to kernel_sha (else reported as null).
-TRAFFIC = {"kernel_sha": None, "kernel": None, "dram_bytes_per_launch": None}
+TRAFFIC = {"kernel_sha": "de579f03c16b5a79", "kernel": "search",
+           "dram_bytes_per_launch": 2060675000 + 238132992 + 46025000 + 2450688}  # front_kernel + search_kernel
 
 
 def kernel_sha() -> str:
@@ -295,7 +296,12 @@ def run_human_sized(args, world, rank, local):
         e.record(stream)
         return e
 
-    p = sa.sa_search_params(front_probes=args.front_probes)
+    if args.front_probes:
+        p, tune = sa.sa_search_params(front_probes=args.front_probes), None
+    else:  # the launch shape and first-pass probes, tuned on a 2,000,000-query sample
+        from paper_1303_3692_gb300 import autotune
+
+        p, tune = autotune.autotune(idx, qb_d, qo_d, sample=2_000_000, use_cache=False)
     p.flags = sa.SA_PARAM_Q_RANGE
     p.q_first, p.q_total = 0, int(w.q_offsets[-1])
     offs = torch.empty(n_q + 1, dtype=torch.int64, device=dev)
@@ -335,7 +341,7 @@ def run_human_sized(args, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": "human-3.1Gbp-int64-q150", "n": int(w.ref.size), "queries_per_step": n_q,
                    "m": 150, "sa_width": 64, "kmer_k": idx.kmer_k, "index_device_bytes": idx.device_bytes,
-                   "l2": "flushed between steps"},
+                   "autotuned": tune["best"] if tune else None, "l2": "flushed between steps"},
         "modes": out, "build_s": build_s, "datagen_s": gen_s, "positions_per_step": total_pos,
         "clocks": clk.summary(),
     }

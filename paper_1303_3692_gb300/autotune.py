@@ -1,11 +1,13 @@
-"""Autotuner for the search kernel's launch shape.
+"""Autotuner for the search's launch shape.
 
 Times sa_search_batch_ex on a sample of a batch for a grid of candidate
 (threads per block, blocks per SM, shared-memory key-table depth, queries per
-warp chunk), checks that every candidate returns identical results, and keeps
-the fastest.  Results are cached in a JSON file keyed by GPU name, the
-references' sizes, the suffix-array width and the batch's length bucket, so a
-serving process tunes once per workload shape.
+warp chunk of the persistent pass, probes of the first pass), checks that
+every candidate returns identical results, and keeps the fastest.  A
+candidate of four values leaves the first pass at the library's default.
+Results are cached in a JSON file keyed by GPU name, the references' sizes,
+the suffix-array width and the batch's length bucket, so a serving process
+tunes once per workload shape.
 """
 from __future__ import annotations
 
@@ -18,10 +20,10 @@ import numpy as np
 
 from . import sa
 
-# (threads per block, blocks per SM, key-table depth, chunk)
-DEFAULT_CANDIDATES: Tuple[Tuple[int, int, int, int], ...] = (
-    (1024, 1, 13, 64), (1024, 1, 12, 64), (1024, 1, 13, 32), (1024, 1, 13, 128),
-    (512, 2, 12, 64), (512, 3, 11, 64), (256, 6, 10, 64), (256, 8, 9, 64),
+# (threads per block, blocks per SM, key-table depth, chunk, first-pass probes)
+DEFAULT_CANDIDATES: Tuple[Tuple[int, ...], ...] = (
+    (1024, 1, 13, 64, 3), (1024, 1, 13, 64, 2), (1024, 1, 13, 64, 4), (1024, 1, 13, 64, 6),
+    (1024, 1, 12, 64, 3), (1024, 1, 13, 32, 3), (512, 2, 12, 64, 3), (256, 6, 10, 64, 3),
 )
 
 LENGTH_BUCKETS = (64, 128, 192, 300, 1 << 62)
@@ -63,7 +65,7 @@ def save_cache(path: str, cache: Dict[str, dict]) -> None:
     os.replace(tmp, path)
 
 
-def pick_best(timings: Iterable[Tuple[Tuple[int, int, int, int], float]]) -> Tuple[Tuple[int, int, int, int], float]:
+def pick_best(timings: Iterable[Tuple[Tuple[int, ...], float]]) -> Tuple[Tuple[int, ...], float]:
     """Fastest candidate; ties go to the earlier one."""
     best = None
     for cand, t in timings:
@@ -75,12 +77,14 @@ def pick_best(timings: Iterable[Tuple[Tuple[int, int, int, int], float]]) -> Tup
 
 
 def params_from(cand: Sequence[int]) -> "sa.sa_search_params":
-    th, bps, depth, chunk = cand
-    return sa.sa_search_params(threads_per_block=th, blocks_per_sm=bps, key_depth=depth, chunk=chunk)
+    th, bps, depth, chunk = cand[:4]
+    fp = cand[4] if len(cand) > 4 else 0
+    return sa.sa_search_params(threads_per_block=th, blocks_per_sm=bps, key_depth=depth, chunk=chunk,
+                               front_probes=fp)
 
 
 def autotune(refs, q_bases, q_offsets, q_ref=None, sample: int = 1_000_000,
-             candidates: Sequence[Tuple[int, int, int, int]] = DEFAULT_CANDIDATES, reps: int = 3,
+             candidates: Sequence[Tuple[int, ...]] = DEFAULT_CANDIDATES, reps: int = 3,
              cache_path: Optional[str] = None, use_cache: bool = True,
              timer: Optional[Callable] = None) -> Tuple["sa.sa_search_params", dict]:
     """(params, report) for this batch shape; q_bases/q_offsets/q_ref on the device."""
@@ -110,7 +114,7 @@ def autotune(refs, q_bases, q_offsets, q_ref=None, sample: int = 1_000_000,
     qr = None if q_ref is None else q_ref[:n_q]
     out = torch.empty((n_q, 3), dtype=torch.int64, device=q_offsets.device)
     ref_result = None
-    timings: List[Tuple[Tuple[int, int, int, int], float]] = []
+    timings: List[Tuple[Tuple[int, ...], float]] = []
     for cand in candidates:
         p = params_from(cand)
         p.flags = sa.SA_PARAM_Q_RANGE

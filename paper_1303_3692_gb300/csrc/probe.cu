@@ -22,7 +22,9 @@ __global__ void chase_kernel(const uint4 *__restrict__ buf, uint64_t n_rec, uint
         ldg32(buf + 2 * idx, &lo, &hi);
         acc = (lo.x ^ hi.w) & 1u;
     }
-    if (acc == 0xFFFFFFFFu) *sink = acc;  // never true; keeps the chain
+    // Practically never true, but the compiler cannot know it, so the whole
+    // chain of reads stays live.
+    if (x == seed) *sink = acc;
 }
 
 }  // namespace

@@ -120,7 +120,7 @@ def test_autotune_picks_working_params_and_caches(env, tmp_path):
     qb, qo, _ = datagen.queries(refs[2], 20000, 501, m=(20, 200), frac_sampled=0.7, subs=(0, 1))
     bases, offs = torch.from_numpy(qb).cuda(), torch.from_numpy(qo).cuda()
     cache = str(tmp_path / "tune.json")
-    cands = ((1024, 1, 12, 64), (512, 2, 11, 32), (256, 4, 10, 64))
+    cands = ((1024, 1, 12, 64), (512, 2, 11, 32, 2), (256, 4, 10, 64, 5))
     p, rep = autotune.autotune(idxs[2], bases, offs, candidates=cands, reps=2, cache_path=cache)
     assert not rep["cached"] and tuple(rep["best"]) in cands and len(rep["all"]) == 3
     a = sa.sa_search_batch(idxs[2], bases, offs, params=p)
