@@ -22,7 +22,7 @@ from . import sa
 
 # (threads per block, blocks per SM, key-table depth, chunk, first-pass probes)
 DEFAULT_CANDIDATES: Tuple[Tuple[int, ...], ...] = (
-    (1024, 1, 13, 64, 3), (1024, 1, 13, 64, 2), (1024, 1, 13, 64, 4), (1024, 1, 13, 64, 6),
+    (1024, 1, 13, 64, 3), (1024, 1, 13, 64, 1), (1024, 1, 13, 64, 2), (1024, 1, 13, 64, 4),
     (1024, 1, 12, 64, 3), (1024, 1, 13, 32, 3), (512, 2, 12, 64, 3), (256, 6, 10, 64, 3),
 )
 

@@ -234,7 +234,7 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     const uint64_t nwords = (total + 31) / 32;
     uint64_t *tq = sc.get<uint64_t>(nwords + SA_TQ_PAD_WORDS);
     uint32_t *tv = sc.get<uint32_t>(nwords + SA_TQ_PAD_WORDS);
-    uint4 *wrec = plain ? nullptr : sc.get<uint4>(2 * n_q);
+    uint4 *wrec = plain ? nullptr : sc.get<uint4>(4 * n_q);
     int *flags = sc.get<int>(4);  // [0] pack error, [1] status, [2] worklist count
     unsigned long long *counter = sc.get<unsigned long long>(1);
     if (sc.failed) return SA_ERR_NOMEM;

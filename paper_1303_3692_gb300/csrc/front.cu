@@ -16,9 +16,9 @@
 //     in all.
 // A query still undecided after that (a bracket wider than the probes could
 // resolve, a query shorter than k, an index without a k-mer table) is
-// appended to a worklist -- a 32-byte record holding a bracket of both
-// bounds, its length, index, reference and first base in the packed batch --
-// which the persistent kernel of search.cu then finishes.
+// appended to a worklist -- a 64-byte record holding a bracket of both
+// bounds, its length, index, reference, first base in the packed batch and
+// first 128 bases -- which the persistent kernel of search.cu then finishes.
 #include "sa_internal.cuh"
 
 namespace sa {
@@ -70,7 +70,7 @@ __device__ __forceinline__ int cmp_entry(const uint64_t w[4], uint32_t m, const 
 template <bool kSingle>
 __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_constant__ SearchLaunch a) {
     __shared__ FrontDesc sdesc[SA_MAX_REFS];
-    __shared__ uint4 s_stage[kFrontThreads / 32][32][2];  // worklist records staged per warp
+    __shared__ uint4 s_stage[kFrontThreads / 32][32][4];  // worklist records staged per warp
     for (unsigned r = threadIdx.x; r < a.n_refs; r += blockDim.x) {
         const RefDesc &d = a.refs.r[r];
         sdesc[r] = FrontDesc{d.text, d.rec, d.krt, (uint32_t)d.n, d.kmer_k};
@@ -88,9 +88,9 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
         if (lane == 0) at = atomicAdd(a.wl_count, cnt);
         at = __shfl_sync(0xFFFFFFFFu, at, 0);
         if (lane < cnt) {
-            uint4 *dst = a.wrec + 2 * (size_t)(at + lane);
-            dst[0] = s_stage[wib][lane][0];
-            dst[1] = s_stage[wib][lane][1];
+            uint4 *dst = a.wrec + 4 * (size_t)(at + lane);
+#pragma unroll
+            for (int j = 0; j < 4; j++) dst[j] = s_stage[wib][lane][j];
         }
         __syncwarp();
     };
@@ -251,6 +251,10 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
                 const uint32_t slot = staged + __popc(bal & lanemask_lt);
                 s_stage[wib][slot][0] = make_uint4(phase == 2 ? lo - 1u : L, phase == 1 ? HR : R, m, (uint32_t)q);
                 s_stage[wib][slot][1] = make_uint4(r, 0u, (uint32_t)qa, (uint32_t)(qa >> 32));
+                s_stage[wib][slot][2] =
+                    make_uint4((uint32_t)w[0], (uint32_t)(w[0] >> 32), (uint32_t)w[1], (uint32_t)(w[1] >> 32));
+                s_stage[wib][slot][3] =
+                    make_uint4((uint32_t)w[2], (uint32_t)(w[2] >> 32), (uint32_t)w[3], (uint32_t)(w[3] >> 32));
             }
             staged += n_new;
             __syncwarp();

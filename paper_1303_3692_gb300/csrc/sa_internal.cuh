@@ -361,7 +361,7 @@ struct SearchLaunch {
     uint64_t total;           // q_off[n_q] - q_off[0]: query ranges past it are invalid
     const uint32_t *q_ref;    // null when n_refs == 1
     uint64_t n_q;
-    uint4 *wrec;              // worklist records, 32 bytes (2 uint4) each, n_q of room
+    uint4 *wrec;              // worklist records, 64 bytes (4 uint4) each, n_q of room
     uint32_t *wl_count;       // device: records in the worklist
     sa_result *out;
     int *pack_err;            // device flag: some query had a non-ACGT byte or bad offsets
@@ -371,10 +371,11 @@ struct SearchLaunch {
     uint32_t threads, blocks, chunk;
     uint32_t front_probes;    // probes per query in the first pass
 };
-// Worklist record of a query the first pass did not finish (32 bytes):
+// Worklist record of a query the first pass did not finish (64 bytes):
 //   {L, R, m, q}            a bracket (L, R) holding both bounds (L = -1 is
 //                           0xFFFFFFFF), the length and the query's index
 //   {ref, 0, qa.lo, qa.hi}  its reference and first base in the packed batch
+//   {w0, w1}, {w2, w3}      its first 128 bases (packed words)
 cudaError_t launch_pack_batch(const SearchLaunch &L, uint64_t *tq, uint32_t *tv, cudaStream_t s);
 cudaError_t launch_front(const SearchLaunch &L, cudaStream_t s);
 cudaError_t launch_search(const SearchLaunch &L, cudaStream_t s);

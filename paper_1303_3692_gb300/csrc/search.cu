@@ -150,15 +150,15 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s for the key-table copy
 // its lane, and every step that touches device memory issues one round of
 // independent loads, so that the 32 lanes of a warp wait for one round per
 // iteration (a lane starting a query never holds up the lanes that probe):
-//   init      read the query's 32-byte worklist record (bracket, length,
-//             index, reference, first base in the packed batch) and its first
-//             64 bases from the packed batch; a query with a k-mer bracket
-//             probes from it, any other descends the key table first;
+//   init      read the query's worklist record (bracket, length, index,
+//             reference, first base in the packed batch, first 64 bases); a
+//             query with a k-mer bracket probes from it, any other descends
+//             the key table first;
 //   descent   compare with the key of level-order node k in shared memory
 //             (k = 0 once the table's depth is passed or the bounds split);
 //   deep      load the suffix record of rank M = L + (R - L)/2 (32 bytes: 112
-//             bases and SA[M]) -- with query bases 64-127 from the packed
-//             batch in the same round -- and compare; only when all 112
+//             bases and SA[M]) -- with query bases 64-127 from the worklist
+//             record in the same round -- and compare; only when all 112
 //             bases tie does the compare continue in the packed text.
 // Ranks are 32-bit modular: L = 0xFFFFFFFF stands for -1, and since every
 // rank is in [-1, n] with n < 2^32 - 1, R - L and L + (R - L)/2 are exact.
@@ -280,21 +280,12 @@ __global__ void __launch_bounds__(Occ<kOcc>::threads, Occ<kOcc>::blocks)
         const bool init = fresh;
         const bool deep = !init && k == 0;
         uint32_t M = L + ((R - L) >> 1);
+        const uint4 *wrec = a.wrec + 4 * (size_t)wi;
         uint4 r0, r1;
-        ldg32_if(init || deep, init ? (const void *)(a.wrec + 2 * (size_t)wi) : (const void *)(REC + 2 * (size_t)M),
-                 &r0, &r1);
-        // query bases 64-127 from the packed batch (L2 hits), beside the record
+        ldg32_if(init || deep, init ? (const void *)wrec : (const void *)(REC + 2 * (size_t)M), &r0, &r1);
+        // the query's bases 0-63 (init) or 64-127 (deep) from its worklist record
         uint64_t x2 = 0, x3 = 0;
-        {
-            const bool want = deep && m > 64u;
-            const uint64_t b = qa + 64u;
-            const uint64_t *p = a.tq + (b >> 5);
-            const uint32_t sh = (uint32_t)(b & 31u) * 2u;
-            const uint64_t t0 = ldg_u64_or(want, p, 0ull), t1 = ldg_u64_or(want, p + 1, 0ull);
-            const uint64_t t2 = ldg_u64_or(want, p + 2, 0ull);
-            x2 = (t0 << sh) | ((t1 >> 1) >> (63u - sh));
-            x3 = (t1 << sh) | ((t2 >> 1) >> (63u - sh));
-        }
+        ldg16_if(init || (deep && m > 64u), wrec + (init ? 2 : 3), &x2, &x3);
 
         if (init) {
             fresh = false;
@@ -313,8 +304,8 @@ __global__ void __launch_bounds__(Occ<kOcc>::threads, Occ<kOcc>::blocks)
             }
             m = r0.z;
             qa = ((uint64_t)r1.w << 32) | r1.z;
-            q0 = text_window(a.tq, qa);  // the query's first 64 bases
-            q1 = text_window(a.tq, qa + 32u);
+            q0 = x2;
+            q1 = x3;
             lcpL = lcpR = 0;
             phase = 0;
             L = r0.x;

@@ -53,7 +53,7 @@ def scratch_bytes(n_q: int, n_bases: int) -> int:
     bases), 64 bytes of worklist room per query, small flags, and 256 bytes of
     alignment per allocation."""
     words = (n_bases + 31) // 32 + 6
-    return 12 * words + 64 * n_q + 64 + 5 * 256
+    return 12 * words + 64 * n_q + 80 + 5 * 256
 
 
 def form_batch(queue: List[Request], max_q: int, max_bases: int, budget: int):
