@@ -57,43 +57,6 @@ __device__ __forceinline__ uint64_t text_window(const uint64_t *__restrict__ T, 
     return (a << sh) | ((c >> 1) >> (63u - sh));
 }
 
-// Compares query P (packed words Q, length m >= 1) with the m-prefix of the
-// suffix starting at text position p, beginning at base `start` (all bases
-// before it are known equal; start < m).  Returns CMP_LESS if P sorts before
-// the suffix, CMP_PREFIX if P is a prefix of it, CMP_GREATER if P sorts after
-// it (a suffix that ends first sorts before P).  *lcp receives the common
-// prefix length, capped at m.  Windows are 32 bases; the query side is read
-// one aligned word at a time.
-__device__ __forceinline__ int cmp_query_suffix(const uint64_t *__restrict__ T, uint64_t n, uint64_t p,
-                                                const uint64_t *__restrict__ Q, uint32_t m,
-                                                uint32_t start, uint32_t *lcp) {
-    uint32_t off = start & ~31u;
-    const int64_t avail0 = (int64_t)n - (int64_t)p;  // bases left in the suffix
-    for (;;) {
-        const int64_t avail = avail0 - (int64_t)off;
-        const uint32_t qlen = min(32u, m - off);
-        const uint32_t tlen = avail <= 0 ? 0u : (avail >= 32 ? 32u : (uint32_t)avail);
-        const uint64_t q = __ldg(Q + (off >> 5));
-        const uint64_t t = tlen ? text_window(T, p + off) : 0ull;
-        const uint64_t x = q ^ t;
-        const uint32_t d = x ? ((uint32_t)__clzll((long long)x) >> 1) : 32u;
-        const uint32_t lim = min(qlen, tlen);
-        if (d < lim) {
-            *lcp = off + d;
-            return q < t ? CMP_LESS : CMP_GREATER;
-        }
-        if (tlen < qlen) {
-            *lcp = off + tlen;
-            return CMP_GREATER;
-        }
-        if (off + 32u >= m) {
-            *lcp = m;
-            return CMP_PREFIX;
-        }
-        off += 32u;
-    }
-}
-
 // Base code of an ASCII byte; returns 4 for a byte outside {ACGTacgt}.
 __device__ __forceinline__ uint32_t base_code(uint32_t c) {
     const uint32_t u = c & 0xDFu;  // fold lower case
@@ -211,24 +174,6 @@ __device__ __forceinline__ void ldg16_if(bool pred, const void *p, uint64_t *x, 
         : "l"(p), "r"((uint32_t)pred));
     *x = a;
     *y = b;
-}
-
-__device__ __forceinline__ uint64_t ldg_u64_or(bool pred, const uint64_t *p, uint64_t v) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t"
-        "@p ld.global.nc.u64 %0, [%1];\n\t}"
-        : "+l"(v)
-        : "l"(p), "r"((uint32_t)pred));
-    return v;
-}
-
-__device__ __forceinline__ uint32_t ldg_u32_or(bool pred, const uint32_t *p, uint32_t v) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t"
-        "@p ld.global.nc.u32 %0, [%1];\n\t}"
-        : "+r"(v)
-        : "l"(p), "r"((uint32_t)pred));
-    return v;
 }
 
 // One window of a compare: q and t hold qlen and tlen bases (tlen may be 0)
