@@ -62,8 +62,8 @@ BYTES_SOURCE = "oracle/bytes_model.py --workload repetitive-100m (k = 14)"
 # DRAM bytes (read + write) per step of the dominant phase from one ncu
 # capture (--set full, 100 Mbp workload), valid only while the kernel sources
 # hash to kernel_sha (else reported as null).
-TRAFFIC = {"kernel_sha": "de579f03c16b5a79", "kernel": "search",
-           "dram_bytes_per_launch": 2060675000 + 238132992 + 46025000 + 2450688}  # front_kernel + search_kernel
+TRAFFIC = {"kernel_sha": "dc46f2fc84e4e26f", "kernel": "search",
+           "dram_bytes_per_launch": 2060411904 + 237837312 + 28388608 + 1850368}  # front_kernel + search_kernel
 
 
 def kernel_sha() -> str:
