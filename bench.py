@@ -62,13 +62,21 @@ BYTES_SOURCE = "oracle/bytes_model.py --workload repetitive-100m (k = 14)"
 # DRAM bytes (read + write) per step of the dominant phase from one ncu
 # capture (--set full, 100 Mbp workload), valid only while the kernel sources
 # hash to kernel_sha (else reported as null).
-TRAFFIC = {"kernel_sha": "dc46f2fc84e4e26f", "kernel": "search",
+TRAFFIC = {"kernel_sha": None, "kernel": "search",
            "dram_bytes_per_launch": 2060411904 + 237837312 + 28388608 + 1850368}  # front_kernel + search_kernel
 
 
-def kernel_sha() -> str:
+# Sources of each phase's kernels (the traffic figure is tied to them).
+PHASE_SOURCES = {
+    "pack_batch_kernel": ("pack.cu", "sa_internal.cuh"),
+    "search": ("front.cu", "search.cu", "sa_internal.cuh"),
+    "locate": ("locate.cu", "sa_internal.cuh"),
+}
+
+
+def kernel_sha(phase: str = "search") -> str:
     h = hashlib.sha256()
-    for f in ("search.cu", "front.cu", "pack.cu", "locate.cu", "sa_internal.cuh"):
+    for f in PHASE_SOURCES[phase]:
         with open(os.path.join(ROOT, "paper_1303_3692_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -594,9 +602,8 @@ def run_ours(args, world, rank, local):
         per_kernel[name] = {"ms": ms, "bytes_per_query": KERNEL_BYTES_PER_QUERY[name], "achieved_gbs": gbs,
                             "frac": gbs / peak}
     dominant = max(phases, key=phases.get)
-    sha = kernel_sha()
     traffic = (TRAFFIC["dram_bytes_per_launch"]
-               if TRAFFIC["kernel_sha"] == sha and TRAFFIC["kernel"] == dominant else None)
+               if TRAFFIC["kernel"] == dominant and TRAFFIC["kernel_sha"] == kernel_sha(dominant) else None)
     roof = {"bound": "hbm", "achieved": per_kernel[dominant]["achieved_gbs"], "peak": peak, "unit": "GB/s",
             "frac": per_kernel[dominant]["frac"], "traffic": traffic, "kernel": dominant,
             "peak_kind": peak_kind, "bytes_per_query": KERNEL_BYTES_PER_QUERY[dominant],

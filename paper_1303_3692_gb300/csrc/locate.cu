@@ -92,35 +92,62 @@ __global__ void __launch_bounds__(1024) scan_partials_kernel(uint64_t *partials,
     if (threadIdx.x == 0) partials[ntiles] = carry_s;
 }
 
-// Item i of thread t covers query tile_base + i * kTileThreads + t (the same
-// queries tile_sums_kernel summed), so every load of results and every store
-// of offsets is coalesced.  Items are scanned in order i = 0..kItems-1.
+// One CTA per tile of kTile queries; warp w owns the tile's queries
+// [w * 256, w * 256 + 256), lane l its queries w * 256 + i * 32 + l for
+// i < kItems, so every load of results and store of offsets is coalesced.  A
+// first pass sums the lane's items; one exchange of warp totals through
+// shared memory (one barrier) places the warps within the tile; a second pass
+// (whose loads hit the caches) places each item within the warp's run by a
+// warp scan (shuffles), writes its offset and copies its positions.
 template <typename IdxT>
-__global__ void __launch_bounds__(kTileThreads) tile_gather_kernel(const __grid_constant__ LocateLaunch a) {
+__global__ void __launch_bounds__(kTileThreads, 3) tile_gather_kernel(const __grid_constant__ LocateLaunch a) {
+    constexpr int kWarps = kTileThreads / 32;
+    __shared__ uint64_t s_warp[kWarps];
     const uint64_t tile_base = (uint64_t)blockIdx.x * kTile;
     const uint64_t ntiles = gridDim.x;
     if (blockIdx.x == ntiles - 1 && threadIdx.x == 0) a.out_offsets[a.n_q] = a.partials[ntiles];
-    uint64_t running = a.partials[blockIdx.x];
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint64_t warp_base = tile_base + (uint64_t)warp * (32 * kItems);
     IdxT *pos = reinterpret_cast<IdxT *>(a.out_pos);
-#pragma unroll 1
+
+    uint64_t lane_sum = 0;
+#pragma unroll
     for (int i = 0; i < kItems; i++) {
-        const uint64_t q = tile_base + (uint64_t)i * kTileThreads + threadIdx.x;
+        const uint64_t q = warp_base + (uint64_t)i * 32 + lane;
+        if (q < a.n_q) lane_sum += kept(a.res[q], a.cap);
+    }
+    uint64_t tot = lane_sum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xFFFFFFFFu, tot, o);
+    if (lane == 0) s_warp[warp] = tot;
+    __syncthreads();
+    uint64_t run = a.partials[blockIdx.x];
+    for (unsigned w = 0; w < warp; w++) run += s_warp[w];
+
+    // Second pass over the items (their results are cache hits now).
+#pragma unroll
+    for (int i = 0; i < kItems; i++) {
+        const uint64_t q = warp_base + (uint64_t)i * 32 + lane;
         sa_result r{0, 0, 0};
         if (q < a.n_q) r = a.res[q];
-        const uint64_t k = q < a.n_q ? kept(r, a.cap) : 0;
-        uint64_t total;
-        const uint64_t off = running + block_exclusive_scan(k, &total);
-        running += total;
+        const uint32_t k = q < a.n_q ? (uint32_t)kept(r, a.cap) : 0u;  // cap is 32-bit
+        uint64_t x = k;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= (unsigned)o) x += y;
+        }
+        const uint64_t off = run + x - k;
+        run += __shfl_sync(0xFFFFFFFFu, x, 31);
         if (q >= a.n_q) continue;
         a.out_offsets[q] = off;
-        if (pos != nullptr && k != 0) {
-            const uint32_t ref = a.q_ref ? a.q_ref[q] : 0u;
-            const RefDesc &d = a.refs.r[ref < a.n_refs ? ref : 0];
-            const IdxT *sa = reinterpret_cast<const IdxT *>(d.sa);
-            const uint64_t kk = (ref < a.n_refs && r.lo <= d.n && k <= d.n - r.lo) ? k : 0;  // never read past SA
-            for (uint64_t t = 0; t < kk; t++) {
-                if (off + t < a.capacity) pos[off + t] = __ldg(sa + r.lo + t);
-            }
+        if (pos == nullptr || k == 0) continue;
+        const uint32_t ref = a.q_ref ? a.q_ref[q] : 0u;
+        const RefDesc &d = a.refs.r[ref < a.n_refs ? ref : 0];
+        const uint64_t kk = (ref < a.n_refs && r.lo <= d.n && k <= d.n - r.lo) ? k : 0;  // never past SA
+        const IdxT *sa = reinterpret_cast<const IdxT *>(d.sa);
+        for (uint64_t t = 0; t < kk; t++) {
+            if (off + t < a.capacity) pos[off + t] = __ldg(sa + r.lo + t);
         }
     }
 }
