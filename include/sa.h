@@ -85,7 +85,8 @@ typedef struct sa_search_params {
     uint32_t flags;             /* SA_PARAM_Q_RANGE: q_first and q_total are given */
     uint32_t front_probes;      /* probes per query in the one-thread-per-query first
                                    pass before a query joins the worklist of the
-                                   persistent kernel (0: 3; at most 64) */
+                                   persistent kernel, at most 64 (0: 1 when some
+                                   index has more suffixes than k-mers, else 3) */
     uint64_t q_first;           /* q_offsets[0] */
     uint64_t q_total;           /* q_offsets[n_q] - q_offsets[0] */
     uint32_t reserved[4];
