@@ -154,6 +154,24 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(seconds: float, dist=None, device=None) -> float:
+    """The slowest rank's time: the job ends when it does."""
+    if dist is None:
+        return seconds
+    import torch
+
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, steps: int, n_q_per_rank: int, seconds: float) -> float:
+    """Queries per second of the whole job.  The path shards by queries with
+    no exchange: every rank holds its own replica of the index and searches
+    its own batch of n_q_per_rank queries per step (weak scaling)."""
+    return world * steps * n_q_per_rank / seconds
+
+
 def build_workload(scale: float):
     from paper_1303_3692_gb300 import datagen
 
@@ -552,12 +570,8 @@ def run_ours(args, world, rank, local):
         "search": statistics.mean(kern_ms),
         "locate": statistics.mean(a.elapsed_time(b) for a, b in zip(k_ends, ends)),
     }
-    total_s = sum(step_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * args.steps * n_q / total_s
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dist, dev)
+    value = job_rate(world, args.steps, n_q, total_s)
 
     # End to end through the C ABI with host (pinned) buffers, copies inside.
     qb_h = torch.from_numpy(w.q_bases).pin_memory()
