@@ -82,7 +82,8 @@ typedef struct sa_search_params {
     uint32_t chunk;             /* queries a warp takes from the global counter at once */
     void *search_events[2];     /* optional cudaEvent_t pair, recorded on the stream right
                                    before and after the search kernel (kernel timing) */
-    uint32_t flags;             /* SA_PARAM_Q_RANGE: q_first and q_total are given */
+    uint32_t flags;             /* SA_PARAM_Q_RANGE: q_first and q_total are given;
+                                   SA_PARAM_REVERSE_COMPLEMENT: search the other strand */
     uint32_t front_probes;      /* probes per query in the one-thread-per-query first
                                    pass before a query joins the worklist of the
                                    persistent kernel, at most 64 (0: 1 when some
@@ -96,6 +97,11 @@ typedef struct sa_search_params {
  * total bases, so a call with device-resident offsets reads nothing back to
  * the host and does not synchronize. */
 #define SA_PARAM_Q_RANGE 0x1u
+/* sa_search_params.flags: search every query's reverse complement (the other
+ * strand: bases in reverse order, A<->T and C<->G) instead of the query, with
+ * the results the reverse-complemented queries would give.  The paper
+ * searches the forward strand only; this flag is an extension. */
+#define SA_PARAM_REVERSE_COMPLEMENT 0x2u
 
 /*
  * sa_build -- index one reference (Section III).

@@ -288,6 +288,7 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     L.blocks = (uint32_t)sms * bps;
     L.chunk = params && params->chunk ? params->chunk : 64;
     L.front_probes = params && params->front_probes ? params->front_probes : default_front_probes(refs, n_refs);
+    L.revcomp = params && (params->flags & SA_PARAM_REVERSE_COMPLEMENT);
     if (L.front_probes > 64) return SA_ERR_ARG;
 
     if ((err = launch_pack_batch(L, tq, tv, s)) != cudaSuccess) return status_from_cuda(err);

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
     for (uint64_t base = warp_first; base < a.n_q; base += stride) {
         const uint64_t q = base + lane;
         const bool live = q < a.n_q;
-        const uint64_t qa = nqa - a.first, qe = nqe - a.first;
+        uint64_t qa = nqa - a.first, qe = nqe - a.first;
         const uint32_t r = nr;
         if (base + stride + lane < a.n_q) {
             nqa = __ldg(a.q_off + base + stride + lane);
@@ -120,6 +120,11 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
         }
         const bool range_ok = live && qa <= qe && qe <= a.total && qe - qa < (1ull << 31);
         if (live && !range_ok) any_bad = true;
+        if (range_ok && a.revcomp) {  // the reverse complement sits at the mirrored range
+            const uint64_t t = a.total - qe;
+            qe = a.total - qa;
+            qa = t;
+        }
         bool ok = range_ok && r < a.n_refs;
         const uint32_t m = ok ? (uint32_t)(qe - qa) : 0u;
 

@@ -86,14 +86,66 @@ __global__ void pack_batch_kernel(const uint8_t *__restrict__ ascii, uint64_t to
     }
 }
 
+// The same for the reverse complement of the whole batch (the other strand):
+// base i of the packed text is the complement of byte total - 1 - i, so query
+// q's reverse complement is bases [total - qe, total - qa) of it.  Word w is
+// packed from the 32 source bytes ending at total - 32 w, then its 2-bit codes
+// are complemented (c -> 3 - c, i.e. every bit flipped) and put in reverse
+// order; its validity mask is reversed the same way.
+__global__ void pack_batch_rc_kernel(const uint8_t *__restrict__ ascii, uint64_t total, uint64_t nwords,
+                                     uint64_t *__restrict__ tq, uint32_t *__restrict__ tv) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords + SA_TQ_PAD_WORDS; w += stride) {
+        if (w >= nwords) {
+            tq[w] = 0;
+            tv[w] = 0;
+            continue;
+        }
+        const uint64_t b0 = w * 32;  // first base of the word in the reverse-complement text
+        uint64_t word = 0;
+        uint32_t mask = 0;
+        if (b0 + 32 <= total) {
+            const uint64_t src = total - b0 - 32;  // its 32 source bytes, in forward order
+            uint32_t bad = 0;
+            const uint64_t fwd = pack_word(ascii, total, src, 32u, &bad);
+            const uint64_t flipped = __brevll(~fwd);  // complement, reverse the bit order
+            // reversing the bits also swapped the two bits of every code: swap them back
+            word = ((flipped >> 1) & 0x5555555555555555ull) | ((flipped & 0x5555555555555555ull) << 1);
+            if (bad) {
+                for (uint32_t j = 0; j < 32; j++)
+                    if (base_code(ascii[src + 31 - j]) > 3) mask |= 1u << j;
+            }
+        } else {  // the last, partial word: bytes one at a time
+            for (uint32_t j = 0; j < 32; j++) {
+                uint32_t code = 0;
+                if (b0 + j < total) {
+                    const uint32_t c = base_code(ascii[total - 1 - b0 - j]);
+                    if (c > 3) {
+                        mask |= 1u << j;
+                    } else {
+                        code = 3u - c;
+                    }
+                }
+                word = (word << 2) | code;
+            }
+        }
+        tq[w] = word;
+        tv[w] = mask;
+    }
+}
+
 cudaError_t launch_pack_batch(const SearchLaunch &L, uint64_t *tq, uint32_t *tv, cudaStream_t s) {
     const int threads = 256;
     const uint64_t want = (L.nwords + SA_TQ_PAD_WORDS + threads - 1) / threads;
     const uint64_t cap = (uint64_t)device_sm_count() * 8;
     const unsigned blocks = (unsigned)(want < cap ? want : cap);
     const bool aligned = ((uintptr_t)L.ascii & 15u) == 0;
-    pack_batch_kernel<<<blocks, threads, 0, s>>>(reinterpret_cast<const uint8_t *>(L.ascii), L.total, L.nwords, tq,
-                                                 tv, aligned);
+    if (L.revcomp)
+        pack_batch_rc_kernel<<<blocks, threads, 0, s>>>(reinterpret_cast<const uint8_t *>(L.ascii), L.total,
+                                                        L.nwords, tq, tv);
+    else
+        pack_batch_kernel<<<blocks, threads, 0, s>>>(reinterpret_cast<const uint8_t *>(L.ascii), L.total, L.nwords,
+                                                     tq, tv, aligned);
     return cudaGetLastError();
 }
 

@@ -315,6 +315,7 @@ struct SearchLaunch {
     uint32_t smem_bytes;      // shared-memory key tables
     uint32_t threads, blocks, chunk;
     uint32_t front_probes;    // probes per query in the first pass
+    bool revcomp;             // search every query's reverse complement (the batch is packed reversed)
 };
 // Worklist record of a query the first pass did not finish (64 bytes):
 //   {L, R, m, q}            a bracket (L, R) holding both bounds (L = -1 is

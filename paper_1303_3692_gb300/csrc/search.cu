@@ -388,10 +388,15 @@ template <typename IdxT>
 __global__ void __launch_bounds__(256) search_plain_kernel(const __grid_constant__ SearchLaunch a) {
     const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= a.n_q) return;
-    const uint64_t a0 = __ldg(a.q_off + q) - a.first;
-    const uint64_t a1 = __ldg(a.q_off + q + 1) - a.first;
+    uint64_t a0 = __ldg(a.q_off + q) - a.first;
+    uint64_t a1 = __ldg(a.q_off + q + 1) - a.first;
     const uint32_t r = a.q_ref ? __ldg(a.q_ref + q) : 0u;
     const bool range_ok = a0 <= a1 && a1 <= a.total && a1 - a0 < (1ull << 31);
+    if (range_ok && a.revcomp) {  // the reverse complement sits at the mirrored range
+        const uint64_t t = a.total - a1;
+        a1 = a.total - a0;
+        a0 = t;
+    }
     bool bad = !range_ok;
     if (range_ok) {  // every base of the query must be one of A, C, G, T
         for (uint64_t b = a0; b < a1; b++)

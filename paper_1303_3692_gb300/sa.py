@@ -35,6 +35,7 @@ SA_W32 = 0x1
 SA_W64 = 0x2
 SA_NO_KMER = 0x4
 SA_PARAM_Q_RANGE = 0x1
+SA_PARAM_REVERSE_COMPLEMENT = 0x2
 SA_LOCATE_NOALLOC_MAX_QUERIES = 1 << 26
 
 _u64 = ctypes.c_uint64

@@ -1,7 +1,7 @@
 """Continuous-batching serving loop over references resident on one GPU.
 
-Requests (a batch of queries against one of the resident references) arrive
-over time.  The server keeps `slots` batches in flight, each on its own CUDA
+Requests (a batch of queries against one of the resident references, and
+how many positions to locate per query: 0 for counts only) arrive over time.  The server keeps `slots` batches in flight, each on its own CUDA
 stream.  Whenever a slot is free it coalesces the waiting requests, oldest
 first, into one batch -- bounded by a query count, a base count and the free
 device memory the library's scratch will need -- and runs that batch as one
@@ -34,7 +34,10 @@ class Request:
     bases: "object"       # pinned uint8 tensor (host) of the concatenated queries
     offsets: np.ndarray   # int64, n + 1 offsets starting at 0
     arrival: float        # seconds since the start of the trace
+    cap: int = 0          # positions to locate per query (0: counts only)
     results: Optional[np.ndarray] = None   # (n, 3) int64: lo, hi, count
+    pos_offsets: Optional[np.ndarray] = None  # (n + 1) int64 when cap > 0
+    positions: Optional[np.ndarray] = None    # located positions, suffix-array order per query
     done: float = math.nan
     status: str = "pending"
 
@@ -56,6 +59,22 @@ def scratch_bytes(n_q: int, n_bases: int) -> int:
     return 12 * words + 64 * n_q + 80 + 5 * 256
 
 
+def kept(counts: np.ndarray, cap: int) -> np.ndarray:
+    """Positions located per query: min(count, cap), none for an invalid query."""
+    return np.where(counts < 0, 0, np.minimum(counts, cap))
+
+
+def split_positions(results: np.ndarray, offs: np.ndarray, pos: np.ndarray, cap_batch: int, cap: int):
+    """A request's positions out of its batch's: the batch located
+    min(count, cap_batch) per query at offs; the request keeps the first
+    min(count, cap) of each.  Returns (offsets (n + 1), positions)."""
+    k = kept(results[:, 2], cap)
+    out_offs = np.zeros(k.size + 1, dtype=np.int64)
+    np.cumsum(k, out=out_offs[1:])
+    idx = np.repeat(offs[:-1], k) + (np.arange(int(out_offs[-1])) - np.repeat(out_offs[:-1], k))
+    return out_offs, pos[idx]
+
+
 def form_batch(queue: List[Request], max_q: int, max_bases: int, budget: int):
     """(taken, rest): the oldest requests whose total queries, bases and
     library scratch stay within max_q, max_bases and the device-memory budget;
@@ -73,7 +92,7 @@ def form_batch(queue: List[Request], max_q: int, max_bases: int, budget: int):
 
 
 class _Slot:
-    def __init__(self, device, max_q: int, max_bases: int):
+    def __init__(self, device, max_q: int, max_bases: int, max_cap: int, pos_dtype):
         import torch
 
         self.stream = torch.cuda.Stream(device=device)
@@ -84,6 +103,12 @@ class _Slot:
         self.h_offsets = torch.empty(max_q + 1, dtype=torch.int64).pin_memory()
         self.h_qref = torch.empty(max(1, max_q), dtype=torch.int32).pin_memory()
         self.h_out = torch.empty((max(1, max_q), 3), dtype=torch.int64).pin_memory()
+        # located positions (when the server locates): every query's first max_cap
+        self.pos_cap = max(1, max_q * max_cap)
+        self.loc_offs = torch.empty(max_q + 1, dtype=torch.int64, device=device) if max_cap else None
+        self.pos = torch.empty(self.pos_cap, dtype=pos_dtype, device=device) if max_cap else None
+        self.h_loc_offs = torch.empty(max_q + 1, dtype=torch.int64).pin_memory() if max_cap else None
+        self.cap = 0
         self.event = None
         self.requests: List[Request] = []
         self.n_q = 0
@@ -93,17 +118,20 @@ class Server:
     def __init__(self, refs: Sequence["sa.Index"], max_batch_queries: int = 1 << 21,
                  max_batch_bases: int = 1 << 28, slots: int = 2, mem_reserve: int = 1 << 30,
                  params: Optional["sa.sa_search_params"] = None,
-                 free_memory: Optional[Callable[[], int]] = None):
+                 free_memory: Optional[Callable[[], int]] = None, max_cap: int = 0):
         import torch
 
         self.refs = list(refs)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.max_q = max_batch_queries
         self.max_bases = max_batch_bases
+        self.max_cap = max_cap
         self.mem_reserve = mem_reserve
         self.params = params
         self.free_memory = free_memory or (lambda: torch.cuda.mem_get_info()[0])
-        self.slots = [_Slot(self.device, max_batch_queries, max_batch_bases) for _ in range(slots)]
+        pos_dtype = torch.int32 if self.refs[0].width == 4 else torch.int64
+        self.slots = [_Slot(self.device, max_batch_queries, max_batch_bases, max_cap, pos_dtype)
+                      for _ in range(slots)]
         self.queue: List[Request] = []
         self.completed: List[Request] = []
         self.batches = 0
@@ -111,7 +139,8 @@ class Server:
 
     # -- admission -----------------------------------------------------
     def submit(self, req: Request) -> None:
-        if req.n > self.max_q or req.nbases > self.max_bases or not 0 <= req.ref < len(self.refs):
+        if (req.n > self.max_q or req.nbases > self.max_bases or not 0 <= req.ref < len(self.refs)
+                or not 0 <= req.cap <= self.max_cap):
             req.status = "rejected"
             req.done = req.arrival
             self.completed.append(req)
@@ -148,9 +177,16 @@ class Server:
             p = sa.sa_search_params() if self.params is None else sa.sa_search_params.from_buffer_copy(self.params)
             p.flags |= sa.SA_PARAM_Q_RANGE
             p.q_first, p.q_total = 0, nb
-            if nq:
+            slot.cap = max((r.cap for r in reqs), default=0)
+            if nq and slot.cap:  # search and locate in one call, up to the batch's largest cap
+                sa.sa_search_locate(self.refs, slot.bases, slot.offsets[:nq + 1], slot.cap, q_ref=slot.qref[:nq],
+                                    out=slot.out[:nq], out_offsets=slot.loc_offs[:nq + 1], out_pos=slot.pos,
+                                    capacity=slot.pos_cap, stream=slot.stream, params=p)
+                slot.h_loc_offs[:nq + 1].copy_(slot.loc_offs[:nq + 1], non_blocking=True)
+            elif nq:
                 sa.sa_search_batch(self.refs, slot.bases, slot.offsets[:nq + 1], q_ref=slot.qref[:nq],
                                    out=slot.out[:nq], stream=slot.stream, params=p)
+            if nq:
                 slot.h_out[:nq].copy_(slot.out[:nq], non_blocking=True)
             slot.event = torch.cuda.Event()
             slot.event.record(slot.stream)
@@ -161,14 +197,21 @@ class Server:
 
     def _finish(self, slot: _Slot, now: float) -> None:
         out = slot.h_out.numpy()
+        pos = offs = None
+        if slot.cap and slot.n_q:
+            offs = slot.h_loc_offs[:slot.n_q + 1].numpy()
+            total = int(offs[-1])
+            pos = slot.pos[:total].cpu().numpy()  # the batch's positions (usually few)
         q = 0
         for r in slot.requests:
             r.results = out[q:q + r.n].copy()
+            if r.cap:
+                r.pos_offsets, r.positions = split_positions(r.results, offs[q:q + r.n + 1], pos, slot.cap, r.cap)
             r.done = now
             r.status = "done"
             q += r.n
             self.completed.append(r)
-        slot.requests, slot.event, slot.n_q = [], None, 0
+        slot.requests, slot.event, slot.n_q, slot.cap = [], None, 0, 0
 
     def poll(self, now: float) -> None:
         for s in self.slots:
@@ -243,18 +286,25 @@ def run_plain(refs: Sequence["sa.Index"], trace: Sequence[Request],
         p = sa.sa_search_params()
         p.flags = sa.SA_PARAM_Q_RANGE
         p.q_first, p.q_total = 0, r.nbases
-        res = sa.sa_search_batch(refs[r.ref], bases, offs, params=p)
+        if r.cap:
+            res, lo_offs, pos = sa.sa_search_locate(refs[r.ref], bases, offs, r.cap, params=p)
+            r.pos_offsets = lo_offs.cpu().numpy()
+            r.positions = pos[:int(r.pos_offsets[-1])].cpu().numpy()
+        else:
+            res = sa.sa_search_batch(refs[r.ref], bases, offs, params=p)
         r.results = res.cpu().numpy()
         r.done = clock() - t0
         r.status = "done"
     return summarize(trace, len(trace))
 
 
-def make_trace(ref_pools, rate: float, duration: float, seed: int, q_range=(1, 100_000)) -> List[Request]:
+def make_trace(ref_pools, rate: float, duration: float, seed: int, q_range=(1, 100_000),
+               caps: Sequence[int] = (0,)) -> List[Request]:
     """Poisson arrivals (mean `rate` per second over `duration` seconds); each
-    request targets a uniformly drawn reference and holds a log-uniform number
-    of queries in q_range, sliced from that reference's pool of pinned queries
-    (ref_pools[r] = (pinned bases tensor, offsets int64 numpy))."""
+    request targets a uniformly drawn reference, holds a log-uniform number of
+    queries in q_range, sliced from that reference's pool of pinned queries
+    (ref_pools[r] = (pinned bases tensor, offsets int64 numpy)), and asks for a
+    locate cap drawn uniformly from caps (0: counts only)."""
     rng = np.random.default_rng(seed)
     t, reqs = 0.0, []
     while True:
@@ -268,5 +318,6 @@ def make_trace(ref_pools, rate: float, duration: float, seed: int, q_range=(1, 1
         n = max(q_range[0], min(n, pool_n))
         s = int(rng.integers(0, pool_n - n + 1))
         o = offs[s:s + n + 1] - offs[s]
-        reqs.append(Request(len(reqs), r, bases[int(offs[s]):int(offs[s + n])], o, t))
+        cap = int(caps[int(rng.integers(0, len(caps)))]) if len(caps) > 1 else int(caps[0])
+        reqs.append(Request(len(reqs), r, bases[int(offs[s]):int(offs[s + n])], o, t, cap=cap))
     return reqs

@@ -57,6 +57,35 @@ def test_serving_results_equal_alone_and_oracle(env):
         assert np.array_equal(a.results, b.results)
 
 
+def test_serving_mixed_locate_caps(env):
+    """Requests with caps 0, 1, 4 and 16 share batches (located up to the
+    batch's largest cap); each request's results and positions equal the
+    request served alone and the oracle's suffix-array positions."""
+    from paper_1303_3692_gb300 import serve
+
+    sa, refs, idxs, pools = env
+    trace = serve.make_trace(pools, rate=4000, duration=0.05, seed=9, q_range=(1, 400), caps=(0, 1, 4, 16))
+    srv = serve.Server(idxs, max_batch_queries=3000, max_batch_bases=3000 * 300, slots=2, max_cap=16)
+    stats = srv.run(trace)
+    assert stats["served"] == len(trace) and stats["batches"] < len(trace)
+    assert {r.cap for r in trace} == {0, 1, 4, 16}
+    osas = [oracle.sa_naive(oracle.normalize(r)) for r in refs]
+    for r in trace:
+        assert np.array_equal(r.results, _alone(sa, idxs[r.ref], r)), r.rid
+        if not r.cap:
+            assert r.positions is None
+            continue
+        bases = r.bases[:r.nbases].cuda() if r.nbases else torch.zeros(1, dtype=torch.uint8, device="cuda")
+        _, offs, pos = sa.sa_search_locate(idxs[r.ref], bases, torch.from_numpy(r.offsets).cuda(), r.cap)
+        offs = offs.cpu().numpy()
+        assert np.array_equal(r.pos_offsets, offs), r.rid
+        assert np.array_equal(r.positions, pos[:int(offs[-1])].cpu().numpy()), r.rid
+        for q in range(0, r.n, 37):
+            lo, hi = int(r.results[q, 0]), int(r.results[q, 1])
+            want = osas[r.ref][lo:lo + min(hi - lo, r.cap)]
+            assert np.array_equal(r.positions[r.pos_offsets[q]:r.pos_offsets[q + 1]].astype(np.int64), want)
+
+
 def test_serving_rejects_and_defers(env):
     from paper_1303_3692_gb300 import serve
 

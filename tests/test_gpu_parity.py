@@ -377,3 +377,38 @@ def test_random_read_rate_probe(sa):
     assert 1e8 < r < 1e13
     with pytest.raises(sa.SAError):
         sa.sa_random_read_rate(64 << 20, 33, 8)
+
+
+def _reverse_complement(qb, qo):
+    """Each query's reverse complement (A<->T, C<->G, order reversed), in place of it."""
+    table = np.arange(256, dtype=np.uint8)
+    for a, b in (("A", "T"), ("C", "G"), ("a", "t"), ("c", "g")):
+        table[ord(a)], table[ord(b)] = ord(b), ord(a)
+    out = np.empty_like(qb)
+    for q in range(qo.size - 1):
+        out[qo[q]:qo[q + 1]] = table[qb[qo[q]:qo[q + 1]][::-1]]
+    return out
+
+
+def test_reverse_complement_flag(sa):
+    """With SA_PARAM_REVERSE_COMPLEMENT every query's reverse complement is
+    searched: the results equal the oracle's on the reverse-complemented
+    queries, and searching the reverse complements of sampled queries with the
+    flag finds the sampled copies again."""
+    ref = datagen.reference(200_000, 91, sd_cover=0.1, tandem_cover=0.05)
+    T = oracle.normalize(ref)
+    osa = oracle.sa_naive(T)
+    idx = sa.sa_build(_dev(ref))
+    qb, qo, smp = datagen.queries(ref, 5000, 92, m=(1, 200), frac_sampled=0.7, subs=(0, 1))
+    rc = _reverse_complement(qb, qo)
+    p = sa.sa_search_params()
+    p.flags = sa.SA_PARAM_REVERSE_COMPLEMENT
+    for fp in (0, 1, 64):  # the first pass alone, and with the persistent pass
+        p.front_probes = fp
+        got = sa.sa_search_batch(idx, _dev(qb), _dev(qo), params=p).cpu().numpy()
+        lo, hi = oracle.search_batch(T, osa, rc, qo, threads=oracle.cpu_threads())
+        assert np.array_equal(got[:, 0], lo) and np.array_equal(got[:, 1], hi)
+        back = sa.sa_search_batch(idx, _dev(rc), _dev(qo), params=p).cpu().numpy()
+        lo2, hi2 = oracle.search_batch(T, osa, qb, qo, threads=oracle.cpu_threads())
+        assert np.array_equal(back[:, 0], lo2) and np.array_equal(back[:, 1], hi2)
+        assert (back[smp, 2] >= 1).sum() > 0

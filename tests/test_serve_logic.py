@@ -70,3 +70,24 @@ def test_autotune_host_logic(tmp_path):
     autotune.save_cache(path, {"k": {"best": [1, 2, 3, 4]}})
     assert autotune.load_cache(path) == {"k": {"best": [1, 2, 3, 4]}}
     assert autotune.load_cache(str(tmp_path / "missing.json")) == {}
+
+
+def test_split_positions_keeps_each_requests_cap():
+    """A batch locates min(count, cap_batch) per query; each request keeps the
+    first min(count, its cap), none for an invalid query (count -1)."""
+    results = np.array([[0, 3, 3], [5, 5, 0], [-1, -1, -1], [7, 9, 2]], dtype=np.int64)
+    offs = np.array([0, 2, 2, 2, 4], dtype=np.int64)  # cap_batch = 2
+    pos = np.array([10, 11, 20, 21], dtype=np.int32)
+    o1, p1 = serve.split_positions(results, offs, pos, 2, 1)
+    assert o1.tolist() == [0, 1, 1, 1, 2] and p1.tolist() == [10, 20]
+    o2, p2 = serve.split_positions(results, offs, pos, 2, 2)
+    assert o2.tolist() == offs.tolist() and p2.tolist() == pos.tolist()
+    assert serve.kept(results[:, 2], 5).tolist() == [3, 0, 0, 2]
+
+
+def test_make_trace_caps_default_keeps_traces():
+    pools = [(np.zeros(100, dtype=np.uint8), np.arange(0, 101, dtype=np.int64))]
+    a = serve.make_trace(pools, rate=1000, duration=0.05, seed=3, q_range=(1, 10))
+    b = serve.make_trace(pools, rate=1000, duration=0.05, seed=3, q_range=(1, 10), caps=(0, 4))
+    assert all(r.cap == 0 for r in a)
+    assert {r.cap for r in b} <= {0, 4}
