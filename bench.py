@@ -62,8 +62,8 @@ BYTES_SOURCE = "oracle/bytes_model.py --workload repetitive-100m (k = 14)"
 # DRAM bytes (read + write) per step of the dominant phase from one ncu
 # capture (--set full, 100 Mbp workload), valid only while the kernel sources
 # hash to kernel_sha (else reported as null).
-TRAFFIC = {"kernel_sha": "c13694acc3e185a1", "kernel": "search",
-           "dram_bytes_per_launch": 2060641024 + 237852416 + 28395776 + 1862400}  # front_kernel + search_kernel
+TRAFFIC = {"kernel_sha": "b52eb447dc121722", "kernel": "search",
+           "dram_bytes_per_launch": 2073794048 + 240993536 + 28380672 + 1843712}  # front_kernel + search_kernel
 
 
 # Sources of each phase's kernels (the traffic figure is tied to them).
