@@ -59,6 +59,10 @@ extern "C" {
 #define SA_W32 0x1u     /* store the suffix array as uint32 (n < 2^32 - 1) */
 #define SA_W64 0x2u     /* store the suffix array as uint64 */
 #define SA_NO_KMER 0x4u /* build no k-mer table (see sa_build) */
+/* build the suffix array on the host by the DC3 construction of Section III
+ * (sa_suffix_array_host) and upload it, instead of prefix doubling on the
+ * GPU; the rest of the index is built on the GPU either way */
+#define SA_BUILD_HOST 0x8u
 /* k of the k-mer table, 1..15, in bits 8-11; 0 there picks k automatically. */
 #define SA_KMER_K(k) ((uint32_t)(k) << 8)
 
@@ -109,7 +113,8 @@ typedef struct sa_search_params {
  * Packs the bases 2 bits each (A=0, C=1, G=2, T=3, base 0 in the most
  * significant bits of each 64-bit word), builds the suffix array of the text
  * on the GPU by prefix doubling (radix sorts of rank pairs; the result is the
- * unique suffix array of Table I's definition), and derives the structures
+ * unique suffix array of Table I's definition) -- or, with SA_BUILD_HOST, on
+ * the host by DC3 as Section III does -- and derives the structures
  * the search reads:
  *  - the key table kept in shared memory (first 64 bases of the suffixes at
  *    ranks floor((2p+1) n / 2^(l+1)), the top levels of the binary search);
@@ -129,7 +134,7 @@ typedef struct sa_search_params {
  *  text   n bytes of bases, host or device memory.
  *  n      number of bases, 1 <= n < 2^32 - 1.
  *  flags  SA_W32 or SA_W64 (exactly one): element width of the suffix array;
- *         optionally SA_NO_KMER or SA_KMER_K(k).
+ *         optionally SA_NO_KMER or SA_KMER_K(k), and SA_BUILD_HOST.
  *  stream CUDA stream (cudaStream_t) or NULL.
  *  out    receives the new index.
  *
@@ -302,6 +307,27 @@ int sa_copy_kmer_table(const sa_index *idx, void *dst, void *stream);
 /* Copies the suffix array (n elements of the index's width) to dst (host or
  * device).  Asynchronous on stream for device/pinned dst. */
 int sa_copy_suffix_array(const sa_index *idx, void *dst, void *stream);
+
+/*
+ * sa_suffix_array_host -- the suffix array of a text by the difference cover
+ * modulo 3 (DC3, Section III: sort the suffixes at positions i mod 3 != 0 by
+ * their leading triples, recursing on the string of triple ranks when two
+ * coincide (Table II ranks them); order the suffixes at i mod 3 == 0 by their
+ * first base and the rank of the next sample suffix; merge the two lists).
+ * Runs on the host CPU, single-threaded, in O(n) time; needs no GPU.
+ *
+ *  text   n ASCII bases (A, C, G, T, either case), host memory.
+ *  n      1 <= n < 2^32 - 1.
+ *  width  4 or 8: element width of sa.
+ *  sa     caller-owned host buffer of n elements: receives the suffix array in
+ *         the order of Table I (a suffix that is a proper prefix of another
+ *         sorts first).
+ *
+ * Errors: SA_ERR_ARG, SA_ERR_BASE (a byte outside the alphabet; sa is then
+ * unspecified), SA_ERR_NOMEM (host memory: up to about 17 n bytes besides sa,
+ * and 4 n more for width 8).
+ */
+int sa_suffix_array_host(const char *text, uint64_t n, uint32_t width, void *sa);
 
 /* Releases the index and its device memory (synchronizes the device first). */
 void sa_free(sa_index *idx);

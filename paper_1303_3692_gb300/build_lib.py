@@ -1,4 +1,4 @@
-"""Compiles the CUDA sources under csrc/ into _lib/libsa.so for sm_103a.
+"""Compiles the CUDA (and host C++) sources under csrc/ into _lib/libsa.so for sm_103a.
 
 Each translation unit is compiled in parallel with nvcc, then linked into one
 shared library with the static CUDA runtime.  Rebuilds only when a source or
@@ -29,14 +29,15 @@ def nvcc() -> str:
 
 
 def sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
 
 def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    deps = (sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
+            + glob.glob(os.path.join(ROOT, "include", "*.h")))
     return any(os.path.getmtime(p) > t for p in deps)
 
 
@@ -47,7 +48,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cc = nvcc()
     objs, procs = [], []
     for src in sources():
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(OUT_DIR, os.path.splitext(os.path.basename(src))[0] + ".o")
         objs.append(obj)
         cmd = [cc, *ARCH, *FLAGS, "-c", src, "-o", obj]
         if verbose:

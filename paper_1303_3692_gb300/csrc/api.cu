@@ -410,7 +410,7 @@ int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_inde
     if (!text || n == 0 || n >= 0xFFFFFFFFull) return SA_ERR_ARG;
     const uint32_t wflags = flags & (SA_W32 | SA_W64);
     if (wflags != SA_W32 && wflags != SA_W64) return SA_ERR_ARG;
-    if (flags & ~(SA_W32 | SA_W64 | SA_NO_KMER | SA_KMER_K(15))) return SA_ERR_ARG;
+    if (flags & ~(SA_W32 | SA_W64 | SA_NO_KMER | SA_BUILD_HOST | SA_KMER_K(15))) return SA_ERR_ARG;
     const uint32_t want_k = (flags >> 8) & 15u;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     sa_index *idx = new (std::nothrow) sa_index();
@@ -452,7 +452,28 @@ int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_inde
             return SA_ERR_BASE;
         }
     }
-    st = build_suffix_array(idx, s);
+    if (flags & SA_BUILD_HOST) {
+        std::vector<char> copy;
+        const char *host_text = text;
+        if (on_device(text)) {
+            try {
+                copy.resize(n);
+            } catch (const std::bad_alloc &) {
+                free_index(idx);
+                return SA_ERR_NOMEM;
+            }
+            cudaError_t err = cudaMemcpyAsync(copy.data(), text, n, cudaMemcpyDeviceToHost, s);
+            if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+            if (err != cudaSuccess) {
+                free_index(idx);
+                return status_from_cuda(err);
+            }
+            host_text = copy.data();
+        }
+        st = build_suffix_array_host(idx, host_text, s);
+    } else {
+        st = build_suffix_array(idx, s);
+    }
     cudaStreamSynchronize(s);
     cudaMemPoolTrimTo(scratch_pool(idx->device), 0);
     if (st == SA_OK) st = alloc_search_arrays(idx);

@@ -1,5 +1,6 @@
-// build.cu -- suffix-array construction on the GPU by prefix doubling, and
-// the sampled-key table.  Off the search path; timed apart from it.
+// build.cu -- suffix-array construction on the GPU by prefix doubling (or the
+// upload of one built on the host by DC3), and the sampled-key table.  Off the
+// search path; timed apart from it.
 //
 // The paper builds its suffix array on the host (the straightforward sort or
 // DC3, Section III).  Here the text is already packed in device memory, so
@@ -16,6 +17,7 @@
 #include <thrust/iterator/counting_iterator.h>
 #include <vector>
 
+#include "dc3.h"
 #include "sa_internal.cuh"
 
 namespace sa {
@@ -203,6 +205,34 @@ int build_suffix_array(sa_index *idx, cudaStream_t s) {
         CK(cudaGetLastError());
     }
     CK(cudaStreamSynchronize(s));
+    return SA_OK;
+}
+
+// The suffix array built on the host by DC3 (Section III's construction, in
+// dc3_host.cpp) from host_text, then uploaded (and widened for 64-bit
+// indexes on the device).
+int build_suffix_array_host(sa_index *idx, const char *host_text, cudaStream_t s) {
+    const uint64_t n = idx->n;
+    std::vector<uint32_t> sa32;
+    try {
+        sa32.resize(n);
+    } catch (const std::bad_alloc &) {
+        return SA_ERR_NOMEM;
+    }
+    const int st = dc3_suffix_array(host_text, n, sa32.data());
+    if (st != SA_OK) return st;
+    if (idx->width == 4) {
+        CK(cudaMemcpyAsync(idx->sa, sa32.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    } else {
+        Pool pool{s};
+        uint32_t *d = pool.get<uint32_t>(n);
+        if (pool.err != cudaSuccess) return SA_ERR_NOMEM;
+        CK(cudaMemcpyAsync(d, sa32.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+        widen_kernel<<<grid_for(n), kThreads, 0, s>>>(d, n, reinterpret_cast<uint64_t *>(idx->sa));
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s));
+    }
     return SA_OK;
 }
 

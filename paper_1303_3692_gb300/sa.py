@@ -34,6 +34,7 @@ SA_ERR_FORMAT = -8
 SA_W32 = 0x1
 SA_W64 = 0x2
 SA_NO_KMER = 0x4
+SA_BUILD_HOST = 0x8
 SA_PARAM_Q_RANGE = 0x1
 SA_PARAM_REVERSE_COMPLEMENT = 0x2
 SA_LOCATE_NOALLOC_MAX_QUERIES = 1 << 26
@@ -80,6 +81,7 @@ SIGNATURES = {
     "sa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sa_version": (_u32, []),
     "sa_random_read_rate": (ctypes.c_int, [_u64, _u32, _u32, ctypes.POINTER(ctypes.c_double), _vp]),
+    "sa_suffix_array_host": (ctypes.c_int, [_vp, _u64, _u32, _vp]),
 }
 
 _lib = None
@@ -186,12 +188,15 @@ class Index:
         sa_save(self, path)
 
 
-def sa_build(text, width: int = 32, stream=None, kmer_k: Optional[int] = None) -> Index:
+def sa_build(text, width: int = 32, stream=None, kmer_k: Optional[int] = None, host_build: bool = False) -> Index:
     """Index one reference (ASCII bases, host or device).  kmer_k: None picks k
-    automatically, 0 builds no k-mer table, 1..15 sets k."""
+    automatically, 0 builds no k-mer table, 1..15 sets k.  host_build: build
+    the suffix array on the host by DC3 instead of on the GPU."""
     flags = SA_W32 if width == 32 else SA_W64 if width == 64 else None
     if flags is None:
         raise ValueError("width must be 32 or 64")
+    if host_build:
+        flags |= SA_BUILD_HOST
     if kmer_k == 0:
         flags |= SA_NO_KMER
     elif kmer_k is not None:
@@ -316,3 +321,14 @@ def sa_random_read_rate(buffer_bytes: int = 4 << 30, threads_per_sm: int = 1024,
     _check(lib().sa_random_read_rate(buffer_bytes, threads_per_sm, steps, ctypes.byref(r), _stream(stream)),
            "sa_random_read_rate")
     return r.value
+
+
+def sa_suffix_array_host(text, width: int = 32) -> np.ndarray:
+    """The suffix array of host bases (numpy uint8 array or CPU tensor) by the
+    library's DC3 construction on the host CPU; needs no GPU."""
+    n = int(text.numel() if torch is not None and isinstance(text, torch.Tensor) else len(text))
+    if width not in (32, 64):
+        raise ValueError("width must be 32 or 64")
+    out = np.empty(max(n, 1), dtype=np.uint32 if width == 32 else np.uint64)
+    _check(lib().sa_suffix_array_host(_ptr(text), n, width // 8, _ptr(out)), "sa_suffix_array_host")
+    return out[:n]

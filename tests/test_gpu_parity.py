@@ -132,6 +132,26 @@ def test_degenerate_texts(sa, text):
     _check_search(sa, idx, T, osa, qb, qo)
 
 
+@pytest.mark.parametrize("width", [32, 64])
+def test_host_dc3_build(sa, width):
+    """SA_BUILD_HOST: the suffix array comes from the host DC3 construction and
+    is uploaded; the index (records, k-mer entries) then answers like any other."""
+    ref = datagen.reference(30011, 77, gc=0.45, sd_cover=0.1, tandem_cover=0.05)
+    ref[15000:21000] = ref[0:6000]  # long exact repeat: deep ties
+    T = oracle.normalize(ref)
+    osa = oracle.sa_naive(T)
+    qb, qo, _ = datagen.queries(ref, 3000, 78, m=(1, 200), frac_sampled=0.7, subs=(0, 1))
+    for text in (torch.from_numpy(ref.copy()), _dev(ref)):  # host and device text
+        idx = sa.sa_build(text, width=width, host_build=True)
+        assert idx.width == width // 8
+        assert np.array_equal(idx.suffix_array().cpu().numpy().astype(np.int64), osa)
+        assert np.array_equal(idx.kmer_table().cpu().numpy(), oracle.kmer_table(T, osa, idx.kmer_k))
+        _check_search(sa, idx, T, osa, qb, qo, plain=False)
+    with pytest.raises(sa.SAError) as e:
+        sa.sa_build(_dev(np.frombuffer(b"ACGTN", np.uint8)), host_build=True)
+    assert e.value.status == sa.SA_ERR_BASE
+
+
 def test_lowercase_equals_uppercase(sa):
     ref = datagen.reference(3000, 3)
     lower = np.frombuffer(ref.tobytes().lower(), dtype=np.uint8)
