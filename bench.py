@@ -687,9 +687,15 @@ def cpu_baseline(w, args):
     t0 = time.perf_counter()
     oracle.search_batch(T, osa, w.q_bases, w.q_offsets[:sample + 1], threads=threads)
     dt = time.perf_counter() - t0
+    # The same oracle on one core, over a quarter of the time budget.
+    sample1 = int(min(n_q, max(1000, (sample / dt) / threads * args.cpu_seconds / 4)))
+    t0 = time.perf_counter()
+    oracle.search_batch(T, osa, w.q_bases, w.q_offsets[:sample1 + 1], threads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": sample / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"first {sample} of {n_q} queries, search only, oracle suffix array by naive sort "
-                      f"({build_s:.1f} s, untimed)"}
+                      f"({build_s:.1f} s, untimed)",
+            "single_core": {"value": sample1 / dt1, "unit": UNIT, "cores": 1, "sample": f"first {sample1} queries"}}
 
 
 def main():
