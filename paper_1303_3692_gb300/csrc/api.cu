@@ -7,6 +7,7 @@
 #include <new>
 #include <vector>
 
+#include "dc3.h"
 #include "sa_internal.cuh"
 
 namespace sa {
@@ -470,7 +471,7 @@ int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_inde
             }
             host_text = copy.data();
         }
-        st = build_suffix_array_host(idx, host_text, s);
+        st = build_suffix_array_host(idx, host_text, stream);
     } else {
         st = build_suffix_array(idx, s);
     }

@@ -211,7 +211,8 @@ int build_suffix_array(sa_index *idx, cudaStream_t s) {
 // The suffix array built on the host by DC3 (Section III's construction, in
 // dc3_host.cpp) from host_text, then uploaded (and widened for 64-bit
 // indexes on the device).
-int build_suffix_array_host(sa_index *idx, const char *host_text, cudaStream_t s) {
+int build_suffix_array_host(sa_index *idx, const char *host_text, void *stream) {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const uint64_t n = idx->n;
     std::vector<uint32_t> sa32;
     try {
