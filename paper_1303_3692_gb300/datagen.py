@@ -241,6 +241,21 @@ MULTI_REF_SIZES = (5_000_000, 12_000_000, 25_000_000, 50_000_000)
 MULTI_REF_GC = (0.38, 0.45, 0.50, 0.62)
 
 
+def paper_shaped(scale: float = 1.0, seed: int = SEED0 + 6, nq: int = 1 << 21) -> Workload:
+    """The shape of the paper's own runs (Section V, Table V): a reference of
+    10^7 bases (here human-like: GC 0.41, 45% repeat families, 3% tandem
+    repeats) and up to 2^21 queries of 1024 bases, half copied exactly from the
+    reference and half random (standing in for the mouse contig's queries,
+    which an exact 1024-base match almost never finds in human sequence).
+    Every prefix of the batch keeps the half-and-half mix."""
+    n = max(20_000, int(10_000_000 * scale))
+    nq = max(1, int(nq * scale))
+    ref = reference(n, seed, gc=0.41, family_cover=0.45, tandem_cover=0.03)
+    qb, qo, smp = queries(ref, nq, seed + 1000, m=1024, frac_sampled=0.5, subs=(0, 0))
+    return Workload("paper-shaped-10Mbp-q1024", ref, qb, qo, smp, cap=0, width=32,
+                    meta={"n": n, "nq": nq, "m": 1024})
+
+
 def multi_genome(scale: float = 1.0, seed: int = SEED0 + 3):
     """4 references (5, 12, 25, 50 Mbp; GC 0.38/0.45/0.50/0.62; 5% segmental
     duplications) and 16,000,000 queries of length U[20,250], each assigned

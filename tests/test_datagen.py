@@ -56,3 +56,12 @@ def test_multi_genome_shapes():
     T = [oracle.normalize(x) for x in refs]
     for q in np.nonzero(smp)[0][:20]:
         assert oracle.bruteforce(T[qref[q]], qb[qo[q]:qo[q + 1]])[0] >= 1
+
+
+def test_paper_shaped_shape():
+    w = datagen.paper_shaped(scale=0.002)
+    assert w.ref.size == 20_000 and np.all(np.diff(w.q_offsets) == 1024)
+    T = oracle.normalize(w.ref)
+    for q in np.nonzero(w.sampled)[0][:10]:
+        assert oracle.bruteforce(T, w.q_bases[w.q_offsets[q]:w.q_offsets[q + 1]])[0] >= 1
+    assert 0.3 < w.sampled.mean() < 0.7

@@ -152,6 +152,17 @@ def test_host_dc3_build(sa, width):
     assert e.value.status == sa.SA_ERR_BASE
 
 
+def test_paper_shaped_1024_base_queries(sa):
+    """The paper's query length (Section V): 1024 bases, half copied exactly from
+    a repeat-rich reference, half random."""
+    w = datagen.paper_shaped(scale=0.1, nq=40960)
+    T = oracle.normalize(w.ref)
+    osa = oracle.sa_naive(T)
+    idx = sa.sa_build(_dev(w.ref))
+    lo, hi = _check_search(sa, idx, T, osa, w.q_bases, w.q_offsets)
+    assert np.all((hi - lo)[w.sampled] >= 1)
+
+
 def test_lowercase_equals_uppercase(sa):
     ref = datagen.reference(3000, 3)
     lower = np.frombuffer(ref.tobytes().lower(), dtype=np.uint8)
