@@ -7,10 +7,22 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dc3.h"
 #include "sa_internal.cuh"
 
 namespace sa {
+
+// An NVTX range over one library call on the calling host thread, so that
+// profilers (ncu --nvtx, Nsight Systems) can select a call's kernels.  Costs a
+// branch when no profiler is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 int status_from_cuda(cudaError_t e) {
     if (e == cudaSuccess) return SA_OK;
@@ -199,6 +211,7 @@ uint32_t fill_ref_table(const sa_index *const *refs, uint32_t n_refs, uint32_t w
 int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_bases, const uint64_t *q_offsets,
                 const uint32_t *q_ref, uint64_t n_q, sa_result *out, void *stream, const sa_search_params *params,
                 bool plain) {
+    NvtxRange range(plain ? "sa_search_plain" : "sa_search");
     uint32_t width = 0;
     int st = check_refs(refs, n_refs, &width);
     if (st) return st;
@@ -406,6 +419,7 @@ using namespace sa;
 extern "C" {
 
 int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_index **out) {
+    NvtxRange range("sa_build");
     if (!out) return SA_ERR_ARG;
     *out = nullptr;
     if (!text || n == 0 || n >= 0xFFFFFFFFull) return SA_ERR_ARG;
@@ -516,6 +530,7 @@ namespace sa {
 int locate_impl(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_ref, const sa_result *res,
                 uint64_t n_q, uint32_t cap, uint64_t *out_offsets, void *out_pos, uint64_t out_pos_capacity,
                 void *stream) {
+    NvtxRange range("sa_locate");
     uint32_t width = 0;
     int st = check_refs(refs, n_refs, &width);
     if (st) return st;
@@ -578,6 +593,7 @@ int sa_search_locate(const sa_index *const *refs, uint32_t n_refs, const char *q
                      const uint32_t *q_ref, uint64_t n_q, sa_result *out, uint32_t cap, uint64_t *out_offsets,
                      void *out_pos, uint64_t out_pos_capacity, void *stream, const sa_search_params *params) {
     using namespace sa;
+    NvtxRange range("sa_search_locate");
     if (!out_offsets || (n_q && !out)) return SA_ERR_ARG;
     const int st = search_impl(refs, n_refs, q_bases, q_offsets, q_ref, n_q, out, stream, params, false);
     if (st && st != SA_ERR_BASE && st != SA_ERR_ARG) return st;
@@ -591,6 +607,7 @@ int sa_search_locate(const sa_index *const *refs, uint32_t n_refs, const char *q
 int sa_locate_noalloc(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_ref, const sa_result *res,
                       uint64_t n_q, uint32_t cap, uint64_t *out_offsets, void *out_pos, uint64_t out_pos_capacity,
                       void *stream) {
+    NvtxRange range("sa_locate_noalloc");
     if (n_q > SA_LOCATE_NOALLOC_MAX_QUERIES) return SA_ERR_CAPACITY;
     uint32_t width = 0;
     int st = check_refs(refs, n_refs, &width);
