@@ -12,10 +12,11 @@
 //      distinct triple by its rank.  The reduced string lists the names of the
 //      mod-1 samples in text order, then those of the mod-2 samples.  If two
 //      samples share a name, its suffix array (recursively) orders them.
-//   3. Sort the suffixes at i mod 3 == 0 by (s[i], rank of the sample at i+1).
+//   3. Sort the suffixes at i mod 3 == 0 by (s[i], rank of the sample at i+1);
+//      Section III's example orders B0 = {0, 3, 6, 9} this way, S9 <= S0 <=
+//      S6 <= S3.
 //   4. Merge the two sorted lists.  A mod-0 suffix and a sample compare by at
-//      most two letters and one sample rank (step 2 of Section III's example
-//      orders B0 = {0, 3, 6, 9} this way).
+//      most two letters and one sample rank.
 // Every step is linear, so one level costs O(n) and the whole recursion O(n).
 #include "dc3.h"
 
