@@ -1,15 +1,17 @@
 #!/usr/bin/env python3
 """Throughput of batched exact matching over a suffix array on one GB300.
 
-Workload (default): a 100 Mbp repetitive reference (iid ACGT, 10% segmental
-duplications, 2% tandem repeats, int32 suffix array) and 10,000,000 queries of
-100 bp (80% sampled from the reference with 0-2 substitutions, 20% random),
-locating up to 64 positions per query.  One step = pack the query batch,
-search every query (the suffix-array interval) and locate its matches -- the
-whole per-batch path -- with the index already built (its build is timed and
-reported apart).  Prints one JSON line.
+Workload (default): a human-genome-sized synthetic reference of 3.1e9 bases
+(GC 0.41, 45% repeat families of 300 bp and 6 kb units at 10-20% divergence,
+3% tandem repeats) with an int64 suffix array, and 1.1e8 queries of 150 bp
+per step (1e8 sampled from the reference with 0-1 substitutions, 1e7
+random), locating up to 16 positions per query.  One step = pack the query
+batch, search every query (the suffix-array interval) and locate its matches
+-- the whole per-batch path -- with the index already built (its build is
+timed and reported apart).  Prints one JSON line.
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+                  [--workload human-sized|repetitive-100m|plain-small|multi-genome|serving|paper-shaped]
 
 --impl reference times the CPU oracle (Alg. 1 on the host cores, the paper's
 serial/OpenMP baseline) on bounded samples of the same workload.
@@ -392,31 +394,133 @@ def run_plain_small(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+HUMAN_WORKLOAD = "human-3.1Gbp-int64-q150-locate16"
+
+
+def _human(args):
+    from paper_1303_3692_gb300 import datagen
+
+    nq = args.human_queries
+    return datagen.human_sized(scale=args.scale, nq_sampled=nq * 10 // 11, nq_random=nq - nq * 10 // 11)
+
+
+def verified_suffix_array(idx, ref):
+    """The index's suffix array on the host, proven correct by the oracle's
+    verifier (a permutation of [0, n) whose adjacent suffixes strictly
+    increase is the unique suffix array): at the 3.1 Gbp size the oracle
+    verifies the GPU-built array instead of rebuilding it.  Returns (T, sa,
+    seconds to verify)."""
+    import oracle
+
+    T = oracle.normalize(ref)
+    sa_h = idx.suffix_array(device="cpu").numpy()
+    t0 = time.perf_counter()
+    code, where = oracle.verify_sa(T, sa_h, threads=oracle.cpu_threads())
+    dt = time.perf_counter() - t0
+    if code != 0:
+        raise RuntimeError(f"suffix array fails the oracle's verifier: code {code} at {where}")
+    return T, sa_h, dt
+
+
+def human_byte_model(T, sa_h, w, k: int, cap: int, sample: int = 20000, seed: int = 7):
+    """Algorithmic bytes and random reads per query of each phase, from the
+    oracle's byte model (oracle.probe_model_bracket: the lockstep search over
+    each query's k-mer bracket, 32-byte records of 112 bases, text windows
+    past them) on a seeded sample of the batch.  The bracket of a query is
+    found by the oracle's binary search for its first k bases and their
+    successor over the verified suffix array (no 4^k table)."""
+    import oracle
+
+    n_q = w.q_offsets.size - 1
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(n_q, size=min(sample, n_q), replace=False))
+    n = T.size
+    tot = dict(m=0.0, entry=0.0, further=0.0, windows=0.0, kept=0.0, count=0.0)
+    for q in pick:
+        P = w.q_bases[w.q_offsets[q]:w.q_offsets[q + 1]]
+        if P.size >= k:
+            x = oracle.kmer_code(P, k)
+            tlo = oracle.kmer_rank(T, sa_h, k, x)
+            thi = oracle.kmer_rank(T, sa_h, k, x + 1) if x + 1 < (1 << (2 * k)) else n
+            pr, wi, tr, lo, hi = oracle.probe_model_bracket(T, sa_h, (tlo, thi), P, d0=13)
+        else:
+            pr, wi, tr, lo, hi = oracle.probe_model_bracket(T, sa_h, None, P, d0=13)
+        tot["m"] += P.size
+        tot["entry"] += tr
+        # the 64-byte k-mer entry carries the bracket's first pivot: that probe costs no record read
+        tot["further"] += max(pr - 1, 0) if tr else pr
+        tot["windows"] += wi
+        tot["kept"] += min(hi - lo, cap)
+        tot["count"] += hi - lo
+    c = float(len(pick))
+    per = {key: v / c for key, v in tot.items()}
+    m = per["m"]
+    search = 8 + m / 4 + m / 8 + 64 * per["entry"] + 32 * per["further"] + 32 * per["windows"] + 24
+    return {
+        "sample": int(c), "k": k,
+        "bytes_per_query": {"pack_batch_kernel": m + m / 4 + m / 8, "search": search,
+                            "locate": 24 + 8 + 16 * per["kept"]},
+        # random sectors per query: 2 for the 64-byte entry, 1 per record, 1 per text window
+        "random_sectors_per_query": 2 * per["entry"] + per["further"] + per["windows"],
+        "entry_reads_per_query": per["entry"], "record_probes_per_query": per["further"],
+        "text_windows_per_query": per["windows"], "mean_count": per["count"], "mean_kept": per["kept"],
+        "source": "oracle.probe_model_bracket over the oracle-verified suffix array",
+    }
+
+
 def run_human_sized(args, world, rank, local):
-    """3.1 Gbp reference (GC 0.41, 45% repeat families, 3% tandem repeats),
-    int64 suffix array; 150 bp queries, 10:1 sampled (0-1 substitutions) to
-    random; count-only steps and locate-up-to-16 steps timed separately."""
+    """The 3.1 Gbp configuration (the default line): a human-genome-sized
+    reference (GC 0.41, 45% repeat families, 3% tandem repeats) with an int64
+    suffix array and 1.1e8 queries of 150 bp per step (10:1 sampled with 0-1
+    substitutions : random).  One step is one sa_search_locate call: pack the
+    batch, search every query and locate up to 16 positions each."""
     import torch
 
     import paper_1303_3692_gb300.sa as sa
-    from paper_1303_3692_gb300 import datagen
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    nq = args.human_queries
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    cap = 16
     t0 = time.perf_counter()
-    w = datagen.human_sized(scale=args.scale, nq_sampled=nq * 10 // 11, nq_random=nq - nq * 10 // 11)
+    w = _human(args)
     gen_s = time.perf_counter() - t0
+    n_q = w.q_offsets.size - 1
+    m_total = int(w.q_offsets[-1])
+    n = int(w.ref.size)
+
+    # Random-read ceiling, measured before the index takes the memory: over
+    # 64 GB, and over a buffer the size of the index (whose reads cross many
+    # more 2 MB pages than the TLBs cover).
+    k_auto = 1
+    while k_auto < 15 and (1 << (2 * (k_auto + 1))) <= 3 * n:
+        k_auto += 1
+    idx_est = n * (8 + 32) + 64 * (1 << (2 * k_auto)) + n // 4
+    free_b = torch.cuda.mem_get_info(dev)[0]
+    at_index = min(idx_est, free_b - (8 << 30)) & ~((1 << 30) - 1)
+    ceiling = {}
+    for size in sorted({64 << 30, at_index}):
+        if size <= 0 or size > free_b - (4 << 30):
+            continue
+        for rb in (32, 64):
+            ceiling[f"{size >> 30}GB_{rb}B"] = sa.sa_random_read_rate(size, 1024, 64, read_bytes=rb) / 1e9
+
     ref_d = torch.from_numpy(w.ref).to(dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     idx = sa.sa_build(ref_d, width=64)
     build_s = time.perf_counter() - t0
     del ref_d
-    n_q = w.q_offsets.size - 1
+    torch.cuda.empty_cache()
+
     qb_d = torch.from_numpy(w.q_bases).to(dev)
     qo_d = torch.from_numpy(w.q_offsets).to(dev)
     res = torch.empty((n_q, 3), dtype=torch.int64, device=dev)
+    offs = torch.empty(n_q + 1, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream()
 
     def lib_event():
@@ -424,56 +528,203 @@ def run_human_sized(args, world, rank, local):
         e.record(stream)
         return e
 
-    if args.front_probes:
-        p, tune = sa.sa_search_params(front_probes=args.front_probes), None
-    else:  # the launch shape and first-pass probes, tuned on a 2,000,000-query sample
+    tune = None
+    if args.autotune:
         from paper_1303_3692_gb300 import autotune
 
         p, tune = autotune.autotune(idx, qb_d, qo_d, sample=2_000_000, use_cache=False)
+    else:
+        p = sa.sa_search_params(front_probes=args.front_probes)
     p.flags = sa.SA_PARAM_Q_RANGE
-    p.q_first, p.q_total = 0, int(w.q_offsets[-1])
-    offs = torch.empty(n_q + 1, dtype=torch.int64, device=dev)
+    p.q_first, p.q_total = 0, m_total
     sa.sa_search_batch(idx, qb_d, qo_d, out=res, params=p)
-    o, ps = sa.sa_locate(idx, res, 16)
+    o, _ = sa.sa_locate(idx, res, cap, out_pos=torch.empty(1, dtype=torch.int64, device=dev), capacity=0)
     total_pos = int(o[-1].item())
+    del o
     pos = torch.empty(max(1, total_pos), dtype=torch.int64, device=dev)
-    del o, ps
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    out = {}
+
+    def timed(mode, steps, clk_needed=False):
+        ts, ks, pk, lc = [], [], [], []
+        for it in range(args.warmup + steps):
+            flush.zero_()
+            a, b = lib_event(), lib_event()
+            k0, k1 = lib_event(), lib_event()
+            p.search_events[0], p.search_events[1] = k0.cuda_event, k1.cuda_event
+            a.record(stream)
+            if mode == "locate16":
+                sa.sa_search_locate(idx, qb_d, qo_d, cap, out=res, out_offsets=offs, out_pos=pos,
+                                    capacity=total_pos, params=p)
+            else:
+                sa.sa_search_batch(idx, qb_d, qo_d, out=res, params=p)
+            b.record(stream)
+            if it >= args.warmup:
+                ts.append((a, b, k0, k1))
+        torch.cuda.synchronize()
+        step = [a.elapsed_time(b) for a, b, _, _ in ts]
+        return {"step_ms_all": step, "ms_per_step": statistics.mean(step),
+                "pack_ms": statistics.mean(a.elapsed_time(k0) for a, _, k0, _ in ts),
+                "search_ms": statistics.mean(k0.elapsed_time(k1) for _, _, k0, k1 in ts),
+                "locate_ms": statistics.mean(k1.elapsed_time(b) for _, b, _, k1 in ts)}
+
     with Clocks(local) as clk:
-        for mode in ("count", "locate16"):
-            ts, ks = [], []
-            for it in range(args.warmup + args.steps):
-                flush.zero_()
-                a, b = lib_event(), lib_event()
-                k0, k1 = lib_event(), lib_event()
-                p.search_events[0], p.search_events[1] = k0.cuda_event, k1.cuda_event
-                a.record(stream)
-                if mode == "locate16":
-                    sa.sa_search_locate(idx, qb_d, qo_d, 16, out=res, out_offsets=offs, out_pos=pos,
-                                        capacity=total_pos, params=p)
-                else:
-                    sa.sa_search_batch(idx, qb_d, qo_d, out=res, params=p)
-                b.record(stream)
-                torch.cuda.synchronize()
-                if it >= args.warmup:
-                    ts.append(a.elapsed_time(b))
-                    ks.append(k0.elapsed_time(k1))
-            out[mode] = {"ms_per_step": statistics.mean(ts), "queries_per_s": n_q / (statistics.mean(ts) / 1e3),
-                         "search_kernel_ms": statistics.mean(ks)}
-    if rank != 0:
-        return
-    line = {
-        "metric": METRIC, "value": out["count"]["queries_per_s"], "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["count"]["ms_per_step"],
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": "human-3.1Gbp-int64-q150", "n": int(w.ref.size), "queries_per_step": n_q,
-                   "m": 150, "sa_width": 64, "kmer_k": idx.kmer_k, "index_device_bytes": idx.device_bytes,
-                   "autotuned": tune["best"] if tune else None, "l2": "flushed between steps"},
-        "modes": out, "build_s": build_s, "datagen_s": gen_s, "positions_per_step": total_pos,
-        "clocks": clk.summary(),
-    }
-    print(json.dumps(line), flush=True)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        main = timed("locate16", args.steps)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+    clocks = clk.summary()
+    count_only = timed("count", max(3, min(args.steps, 10)))
+    total_s = max_over_ranks(sum(main["step_ms_all"]) / 1e3, dist, dev)
+    value = job_rate(world, args.steps, n_q, total_s)
+
+    # End to end through the C ABI from pinned host buffers: the batch's
+    # bases and offsets go up and results, offsets and positions come back
+    # inside the timed region.
+    qb_h = torch.from_numpy(w.q_bases).pin_memory()
+    qo_h = torch.from_numpy(w.q_offsets).pin_memory()
+    res_h = torch.empty((n_q, 3), dtype=torch.int64).pin_memory()
+    offs_h = torch.empty(n_q + 1, dtype=torch.int64).pin_memory()
+    pos_h = torch.empty(max(1, total_pos), dtype=torch.int64).pin_memory()
+    del qb_d
+    torch.cuda.empty_cache()
+
+    def e2e_step():
+        sa.sa_search_locate(idx, qb_h, qo_h, cap, out=res_h, out_offsets=offs_h, out_pos=pos_h,
+                            capacity=total_pos)
+        torch.cuda.synchronize()
+
+    e2e_step()
+    e2e_t = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(e2e_t)
+    h2d = int(qb_h.numel() + qo_h.numel() * 8)
+    d2h = int(res_h.numel() * 8 + offs_h.numel() * 8 + total_pos * 8)
+    # the plain pinned copy rate of this link, for context
+    probe_d = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(4):
+        probe_d.copy_(qb_h[:1 << 30], non_blocking=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    h2d_gbs = 4 * (1 << 30) / (a.elapsed_time(b) / 1e3) / 1e9
+    del probe_d
+    qb_d = torch.from_numpy(w.q_bases).to(dev)
+
+    # The plain one-thread-per-query kernel (Alg. 1) on the first 16M queries.
+    n_plain = min(n_q, 16_000_000)
+    plain_ms = []
+    for _ in range(2):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sa.sa_search_batch_plain(idx, qb_d, qo_d[:n_plain + 1], out=res[:n_plain])
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain_ms.append(a.elapsed_time(b))
+    plain_qps = n_plain / (min(plain_ms) / 1e3)
+    del qb_d
+    torch.cuda.empty_cache()
+
+    line = None
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        T, sa_h, verify_s = verified_suffix_array(idx, w.ref)
+        model = human_byte_model(T, sa_h, w, idx.kmer_k, cap)
+        phases = {"pack_batch_kernel": main["pack_ms"], "search": main["search_ms"], "locate": main["locate_ms"]}
+        per_kernel = {}
+        for name, ms in phases.items():
+            gbs = model["bytes_per_query"][name] * n_q / (ms / 1e3) / 1e9
+            per_kernel[name] = {"ms": ms, "bytes_per_query": model["bytes_per_query"][name], "achieved_gbs": gbs,
+                                "frac": gbs / peak}
+        dominant = max(phases, key=phases.get)
+        traffic = (HUMAN_TRAFFIC["dram_bytes_per_launch"]
+                   if HUMAN_TRAFFIC["kernel"] == dominant and HUMAN_TRAFFIC["kernel_sha"] == kernel_sha(dominant)
+                   else None)
+        sect = model["random_sectors_per_query"] * n_q / (phases["search"] / 1e3) / 1e9
+        rr64 = ceiling.get("64GB_32B")
+        rrix = ceiling.get(f"{at_index >> 30}GB_32B")
+        roof = {"bound": "hbm", "achieved": per_kernel[dominant]["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                "frac": per_kernel[dominant]["frac"], "traffic": traffic, "kernel": dominant, "peak_kind": peak_kind,
+                "bytes_per_query": model["bytes_per_query"][dominant], "bytes_source": model["source"],
+                "per_kernel": per_kernel,
+                "random_reads": {"kernel": "search", "achieved": sect, "unit": "G sectors/s",
+                                 "sectors_per_query": model["random_sectors_per_query"],
+                                 "peak_64GB": rr64, "frac_64GB": sect / rr64 if rr64 else None,
+                                 "peak_at_index_size": rrix, "index_size_GB": at_index >> 30,
+                                 "frac_at_index_size": sect / rrix if rrix else None,
+                                 "ceilings_G_reads_per_s": ceiling,
+                                 "peak_source": "sa_random_read_rate_ex(size, 1024 threads/SM, 64 dependent reads)"},
+                "model": model}
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline_sa(T, sa_h, w, args, f"oracle-verified GPU suffix array ({verify_s:.1f} s to verify)")
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": HUMAN_WORKLOAD, "n": n, "queries_per_step": n_q, "m": 150, "locate_cap": cap,
+                       "sa_width": 64, "kmer_k": idx.kmer_k, "index_device_bytes": idx.device_bytes,
+                       "autotuned": tune["best"] if tune else None,
+                       "l2": "flushed between steps (256 MB write, outside the step events); inputs > L2",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "query_bases_per_s": value * (m_total / n_q),
+            "phase_ms": phases, "step_ms_all": main["step_ms_all"],
+            "count_only": {"ms_per_step": count_only["ms_per_step"],
+                           "queries_per_s": n_q / (count_only["ms_per_step"] / 1e3),
+                           "search_ms": count_only["search_ms"]},
+            "build_s": build_s, "datagen_s": gen_s, "positions_per_step": total_pos,
+            "plain_kernel": {"queries": n_plain, "ms": min(plain_ms), "queries_per_s": plain_qps,
+                             "search_speedup": (n_q / ((phases["pack_batch_kernel"] + phases["search"]) / 1e3))
+                             / plain_qps},
+            "e2e": {"value": n_q / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e2e_s * 1e3, "pinned_h2d_gbs": h2d_gbs,
+                    "upload_bound_ms": h2d / (h2d_gbs * 1e9) * 1e3},
+            "gpu_launches": args.steps * 6,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# DRAM bytes (read + write) per launch of the 3.1 Gbp search phase from one ncu
+# capture, valid only while the kernel sources hash to kernel_sha.
+HUMAN_TRAFFIC = {"kernel_sha": "", "kernel": "search", "dram_bytes_per_launch": None}
+
+
+def cpu_baseline_sa(T, sa_h, w, args, sa_note: str):
+    """The oracle (Alg. 1 on all host cores, then on one core) on a bounded
+    sample of the batch against a given (verified) suffix array."""
+    import oracle
+
+    threads = oracle.cpu_threads()
+    n_q = w.q_offsets.size - 1
+    probe = min(n_q, 20000)
+    t0 = time.perf_counter()
+    oracle.search_batch(T, sa_h, w.q_bases, w.q_offsets[:probe + 1], threads=threads)
+    rate = probe / max(1e-9, time.perf_counter() - t0)
+    sample = int(min(n_q, max(probe, rate * args.cpu_seconds)))
+    t0 = time.perf_counter()
+    oracle.search_batch(T, sa_h, w.q_bases, w.q_offsets[:sample + 1], threads=threads)
+    dt = time.perf_counter() - t0
+    sample1 = int(min(n_q, max(1000, (sample / dt) / threads * args.cpu_seconds / 4)))
+    t0 = time.perf_counter()
+    oracle.search_batch(T, sa_h, w.q_bases, w.q_offsets[:sample1 + 1], threads=1)
+    dt1 = time.perf_counter() - t0
+    return {"value": sample / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {sample} of {n_q} queries, search only (Alg. 1), {sa_note}",
+            "single_core": {"value": sample1 / dt1, "unit": UNIT, "cores": 1, "sample": f"first {sample1} queries"}}
 
 
 def run_serving(args, world, rank, local):
@@ -530,6 +781,59 @@ def run_serving(args, world, rank, local):
         "saturated": {"batched": sat_stats, "plain_per_request": sat_plain_stats,
                       "throughput_gain": sat_stats["queries_per_s"] / sat_plain_stats["queries_per_s"]},
         "build_s": build_s, "datagen_s": gen_s, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_human(args, world, rank, local):
+    """The reference arm on the 3.1 Gbp workload: the oracle as it stands
+    (Alg. 1 on this host's cores) on bounded samples of the batch.  The oracle
+    cannot sort 3.1e9 suffixes in minutes, so its suffix array is the one the
+    GPU builds, proven to be the unique suffix array by the oracle's own
+    verifier first; only the oracle's search is timed."""
+    import torch
+
+    import oracle
+    import paper_1303_3692_gb300.sa as sa
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = _human(args)
+    t0 = time.perf_counter()
+    idx = sa.sa_build(torch.from_numpy(w.ref).to(dev), width=64)
+    build_s = time.perf_counter() - t0
+    T, sa_h, verify_s = verified_suffix_array(idx, w.ref)
+    del idx
+    threads = oracle.cpu_threads()
+    n_q = w.q_offsets.size - 1
+    probe = min(n_q, 20000)
+    t0 = time.perf_counter()
+    oracle.search_batch(T, sa_h, w.q_bases, w.q_offsets[:probe + 1], threads=threads)
+    rate = probe / max(1e-9, time.perf_counter() - t0)
+    sample = int(min(n_q, max(probe, rate * args.ref_step_seconds)))
+    qo = w.q_offsets[:sample + 1]
+    for _ in range(args.warmup):
+        oracle.search_batch(T, sa_h, w.q_bases, qo, threads=threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.search_batch(T, sa_h, w.q_bases, qo, threads=threads)
+        times.append(time.perf_counter() - t0)
+    per_step = statistics.mean(times)
+    value = sample / per_step
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": HUMAN_WORKLOAD, "n": int(w.ref.size), "queries_per_step": sample, "m": 150,
+                   "note": "search only (Alg. 1 on the CPU; the oracle has no locate kernel to time)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"first {sample} of {n_q} queries per step, against the GPU-built suffix "
+                                   f"array after the oracle's verifier proved it ({verify_s:.1f} s; build "
+                                   f"{build_s:.1f} s, untimed)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -810,9 +1114,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=6.0)
-    ap.add_argument("--workload", choices=["repetitive-100m", "plain-small", "multi-genome", "serving",
-                                           "human-sized", "paper-shaped"],
-                    default="repetitive-100m")
+    ap.add_argument("--workload", choices=["human-sized", "repetitive-100m", "plain-small", "multi-genome",
+                                           "serving", "paper-shaped"],
+                    default="human-sized")
+    ap.add_argument("--autotune", action="store_true", help="tune the launch shape before timing (human-sized)")
     ap.add_argument("--human-queries", type=int, default=110_000_000,
                     help="queries per step of the 3.1 Gbp workload (100M sampled + 10M random)")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
@@ -822,7 +1127,10 @@ def main():
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":
-        run_reference(args, world, rank)
+        if args.workload == "human-sized":
+            run_reference_human(args, world, rank, local)
+        else:
+            run_reference(args, world, rank)
     elif args.workload == "multi-genome":
         run_multi_genome(args, world, rank, local)
     elif args.workload == "plain-small":

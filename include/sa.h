@@ -94,8 +94,30 @@ typedef struct sa_search_params {
                                    index has more suffixes than k-mers, else 3) */
     uint64_t q_first;           /* q_offsets[0] */
     uint64_t q_total;           /* q_offsets[n_q] - q_offsets[0] */
-    uint32_t reserved[4];
+    int32_t *device_status;     /* optional caller-owned int32 in device memory: at the end
+                                   of the call's work on the stream the library writes the
+                                   call's status there (see "Device status" below) */
+    uint32_t reserved[2];
 } sa_search_params;
+
+/*
+ * Device status.  A call whose outputs are device memory returns as soon as
+ * its work is queued, so it cannot return what the kernels find.  Given
+ * sa_search_params.device_status, the call queues one more one-thread kernel
+ * that stores, in order of precedence:
+ *   SA_ERR_TIMEOUT   a bounded device-side wait (the persistent kernel's copy
+ *                    of the key tables into shared memory, 2 s) ran out; the
+ *                    results of the queries that kernel was to finish are
+ *                    then undefined;
+ *   SA_ERR_BASE      some query holds a byte outside {A,C,G,T,a,c,g,t} or has
+ *                    offsets outside the batch (its result is all-ones);
+ *   SA_ERR_ARG       some query names a reference id >= n_refs (all-ones);
+ *   SA_ERR_CAPACITY  (sa_search_locate only) out_pos was too small for the
+ *                    positions: out_offsets[n_q] > out_pos_capacity;
+ *   SA_OK            otherwise.
+ * The word is valid once the stream has reached the end of the call.  With
+ * host outputs the call returns the same status itself.
+ */
 
 /* sa_search_params.flags: the caller states q_offsets[0] and the batch's
  * total bases, so a call with device-resident offsets reads nothing back to
@@ -106,6 +128,12 @@ typedef struct sa_search_params {
  * the results the reverse-complemented queries would give.  The paper
  * searches the forward strand only; this flag is an extension. */
 #define SA_PARAM_REVERSE_COMPLEMENT 0x2u
+/* sa_search_params.flags, for testing the error path only: the persistent
+ * kernel's bounded wait for its key tables gives up at once, as if its limit
+ * had run out (the kernel still waits, bounded, for the copies it started
+ * before it exits).  The call then reports SA_ERR_TIMEOUT and the results of
+ * the queries that kernel was to finish are undefined. */
+#define SA_PARAM_EXPIRE_WAITS 0x4u
 
 /*
  * sa_build -- index one reference (Section III).
@@ -213,10 +241,17 @@ int sa_search_batch_plain(const sa_index *const *refs, uint32_t n_refs, const ch
  *  out_pos    positions, element width = the indexes' suffix-array width
  *             (uint32 or uint64); may be NULL to compute only the offsets.
  *  out_pos_capacity  elements available in out_pos.  Positions whose slot
- *             is at or beyond it are not written; the caller detects this
- *             as out_offsets[n_q] > out_pos_capacity.
+ *             is at or beyond it are not written.
  *
- * Errors: SA_ERR_ARG, SA_ERR_NOMEM, SA_ERR_CUDA.
+ * A query is truncated when res[i].count > cap: it then keeps the first cap
+ * positions of its interval.  When out_pos is too small (out_offsets[n_q] >
+ * out_pos_capacity) the positions that fit are written and, if out_offsets or
+ * out_pos is host memory (the call then reads the total back and
+ * synchronizes), the call returns SA_ERR_CAPACITY; with both in device memory
+ * the call is asynchronous and the caller checks out_offsets[n_q] (or uses
+ * sa_search_locate with a device status word).
+ *
+ * Errors: SA_ERR_ARG, SA_ERR_CAPACITY (see above), SA_ERR_NOMEM, SA_ERR_CUDA.
  */
 int sa_locate(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_ref,
               const sa_result *res, uint64_t n_q, uint32_t cap, uint64_t *out_offsets,
@@ -230,7 +265,9 @@ int sa_locate(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_re
  *  cap ... out_pos_capacity  as for sa_locate.
  *
  * Errors: as sa_search_batch (an invalid query gets the all-ones result and
- * no positions; the other queries are located) and sa_locate.
+ * no positions; the other queries are located) and sa_locate.  With
+ * params->device_status the word also reports SA_ERR_CAPACITY when out_pos is
+ * too small.
  */
 int sa_search_locate(const sa_index *const *refs, uint32_t n_refs, const char *q_bases,
                      const uint64_t *q_offsets, const uint32_t *q_ref, uint64_t n_q,
@@ -298,6 +335,15 @@ int sa_index_info(const sa_index *idx, uint64_t *n, uint32_t *width, uint32_t *k
  */
 int sa_random_read_rate(uint64_t buffer_bytes, uint32_t threads_per_sm, uint32_t steps, double *reads_per_s,
                         void *stream);
+
+/* sa_random_read_rate with the size of one read: read_bytes (32, 64, 128,
+ * 256 or 512) contiguous bytes starting on a read_bytes boundary, fetched as
+ * independent 32-byte loads on which the next address depends.  Whether a
+ * wider read costs one DRAM row activation or several decides how much a
+ * search gains from wider nodes.  *reads_per_s counts reads, not sectors.
+ * Errors: as sa_random_read_rate, and SA_ERR_ARG for any other read_bytes. */
+int sa_random_read_rate_ex(uint64_t buffer_bytes, uint32_t threads_per_sm, uint32_t steps, uint32_t read_bytes,
+                           double *reads_per_s, void *stream);
 
 /* Copies the k-mer table's counts kmer[x] (4^k + 1 uint32, the last = n) to
  * dst (host or device; a host copy synchronizes the stream).  SA_ERR_ARG if

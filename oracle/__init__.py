@@ -71,6 +71,11 @@ def _load():
         lib.oracle_probe_model_kmer.argtypes = [_p, _i64, _p, _p, ctypes.c_int, ctypes.c_int, _p, _i64,
                                                 _pi64, _pi64, _pi64, _pi64, _pi64]
         lib.oracle_probe_model_kmer.restype = None
+        lib.oracle_kmer_rank.argtypes = [_p, _i64, _p, ctypes.c_int, _i64]
+        lib.oracle_kmer_rank.restype = _i64
+        lib.oracle_probe_model_bracket.argtypes = [_p, _i64, _p, ctypes.c_int, _i64, _i64, ctypes.c_int, _p, _i64,
+                                                   _pi64, _pi64, _pi64, _pi64, _pi64]
+        lib.oracle_probe_model_bracket.restype = None
         _lib = lib
     return _lib
 
@@ -79,6 +84,13 @@ def _u8(a) -> np.ndarray:
     if isinstance(a, (bytes, bytearray, str)):
         a = np.frombuffer(a.encode() if isinstance(a, str) else bytes(a), dtype=np.uint8)
     return np.ascontiguousarray(a, dtype=np.uint8)
+
+
+def _i64sa(sa) -> np.ndarray:
+    """A suffix array as int64 without a copy where it already is 64-bit."""
+    if isinstance(sa, np.ndarray) and sa.dtype == np.uint64 and sa.flags.c_contiguous:
+        return sa.view(np.int64)
+    return np.ascontiguousarray(sa, dtype=np.int64)
 
 
 def _ptr(a: np.ndarray):
@@ -109,7 +121,7 @@ def sa_naive(T) -> np.ndarray:
 
 def ranks(sa) -> np.ndarray:
     """1-based inverse suffix array (Table III)."""
-    sa = np.ascontiguousarray(sa, dtype=np.int64)
+    sa = _i64sa(sa)
     r = np.empty_like(sa)
     _load().oracle_ranks(_ptr(sa), sa.size, _ptr(r))
     return r
@@ -119,7 +131,7 @@ def verify_sa(T, sa, threads: int = 1):
     """(code, index): code 0 iff sa is the suffix array of T (permutation whose
     adjacent suffixes strictly increase); 1 out of range, 2 repeat, 3 order."""
     T = _u8(T)
-    sa = np.ascontiguousarray(sa, dtype=np.int64)
+    sa = _i64sa(sa)
     if sa.size != T.size:
         return (1, -1)
     w = _i64(-1)
@@ -130,7 +142,7 @@ def verify_sa(T, sa, threads: int = 1):
 def search(T, sa, P):
     """Alg. 1 on the CPU for one query; returns half-open (lo, hi)."""
     T, P = _u8(T), _u8(P)
-    sa = np.ascontiguousarray(sa, dtype=np.int64)
+    sa = _i64sa(sa)
     lo, hi = _i64(), _i64()
     _load().oracle_search(_ptr(T), T.size, _ptr(sa), _ptr(P), P.size,
                           ctypes.byref(lo), ctypes.byref(hi))
@@ -148,7 +160,7 @@ def rank_count(T, P):
 def search_batch(T, sa, Q, qoff, threads: int = 1):
     """Alg. 1 over a batch; Q concatenated bases, qoff (nq+1) offsets."""
     T, Q = _u8(T), _u8(Q)
-    sa = np.ascontiguousarray(sa, dtype=np.int64)
+    sa = _i64sa(sa)
     qoff = np.ascontiguousarray(qoff, dtype=np.int64)
     nq = qoff.size - 1
     lo = np.empty(nq, dtype=np.int64)
@@ -187,7 +199,7 @@ def sort_positions(T, pos) -> np.ndarray:
 
 
 def locate(sa, lo: int, hi: int, cap: int) -> np.ndarray:
-    sa = np.ascontiguousarray(sa, dtype=np.int64)
+    sa = _i64sa(sa)
     k = max(0, min(hi - lo, cap))
     out = np.empty(k, dtype=np.int64)
     _load().oracle_locate(_ptr(sa), lo, hi, cap, _ptr(out))
@@ -197,7 +209,7 @@ def locate(sa, lo: int, hi: int, cap: int) -> np.ndarray:
 def probe_model(T, sa, P, d0: int = 13):
     """(probes, chunks, lo, hi) of the lockstep search byte model for one query."""
     T, P = _u8(T), _u8(P)
-    sa = np.ascontiguousarray(sa, dtype=np.int64)
+    sa = _i64sa(sa)
     pr, ch, lo, hi = _i64(), _i64(), _i64(), _i64()
     _load().oracle_probe_model(_ptr(T), T.size, _ptr(sa), _ptr(P), P.size, int(d0),
                                ctypes.byref(pr), ctypes.byref(ch), ctypes.byref(lo), ctypes.byref(hi))
@@ -207,7 +219,7 @@ def probe_model(T, sa, P, d0: int = 13):
 def kmer_table(T, sa, k: int) -> np.ndarray:
     """table[x] = number of suffixes sorting before the k-base string x; table[4^k] = n."""
     T = _u8(T)
-    sa = np.ascontiguousarray(sa, dtype=np.int64)
+    sa = _i64sa(sa)
     out = np.empty((1 << (2 * k)) + 1, dtype=np.int64)
     _load().oracle_kmer_table(_ptr(T), T.size, _ptr(sa), int(k), _ptr(out))
     return out
@@ -216,10 +228,40 @@ def kmer_table(T, sa, k: int) -> np.ndarray:
 def probe_model_kmer(T, sa, table, k: int, P, d0: int = 13):
     """(probes, text windows, table reads, lo, hi) of the k-mer + record search model."""
     T, P = _u8(T), _u8(P)
-    sa = np.ascontiguousarray(sa, dtype=np.int64)
+    sa = _i64sa(sa)
     tab = None if table is None else np.ascontiguousarray(table, dtype=np.int64)
     pr, wi, tr, lo, hi = _i64(), _i64(), _i64(), _i64(), _i64()
     _load().oracle_probe_model_kmer(_ptr(T), T.size, _ptr(sa), None if tab is None else _ptr(tab), int(k), int(d0),
                                     _ptr(P), P.size, ctypes.byref(pr), ctypes.byref(wi), ctypes.byref(tr),
                                     ctypes.byref(lo), ctypes.byref(hi))
+    return pr.value, wi.value, tr.value, lo.value, hi.value
+
+
+def kmer_rank(T, sa, k: int, x: int) -> int:
+    """Number of suffixes sorting before the k-base string x (one table entry)."""
+    T = _u8(T)
+    sa = _i64sa(sa)
+    return int(_load().oracle_kmer_rank(_ptr(T), T.size, _ptr(sa), int(k), int(x)))
+
+
+def kmer_code(P, k: int) -> int:
+    """The first k bases of P as a base-4 number (A=0 C=1 G=2 T=3)."""
+    x = 0
+    for c in bytes(_u8(P)[:k]):
+        x = 4 * x + b"ACGT".index(c)
+    return x
+
+
+def probe_model_bracket(T, sa, bracket, P, d0: int = 13):
+    """The k-mer + record search model for one query given its bracket
+    (tlo, thi) = (table[x], table[x + 1]), or None for a query without one:
+    (probes, text windows, table reads, lo, hi)."""
+    T, P = _u8(T), _u8(P)
+    sa = _i64sa(sa)
+    has = bracket is not None
+    tlo, thi = bracket if has else (0, 0)
+    pr, wi, tr, lo, hi = _i64(), _i64(), _i64(), _i64(), _i64()
+    _load().oracle_probe_model_bracket(_ptr(T), T.size, _ptr(sa), int(has), int(tlo), int(thi), int(d0), _ptr(P),
+                                       P.size, ctypes.byref(pr), ctypes.byref(wi), ctypes.byref(tr),
+                                       ctypes.byref(lo), ctypes.byref(hi))
     return pr.value, wi.value, tr.value, lo.value, hi.value

@@ -139,34 +139,78 @@ static void *verify_worker(void *p)
     return NULL;
 }
 
+struct perm_job {
+    const int64_t *sa;
+    int64_t n, a, b, where;
+    uint8_t *seen;
+    int rc;
+};
+
+/* Marks the values of sa[a..b) in seen; a value out of range, or one already
+ * marked (by this thread or another), is reported. */
+static void *perm_worker(void *p)
+{
+    struct perm_job *j = (struct perm_job *)p;
+    for (int64_t k = j->a; k < j->b; k++) {
+        int64_t v = j->sa[k];
+        if (v < 0 || v >= j->n) {
+            j->rc = 1;
+            j->where = k;
+            return NULL;
+        }
+        if (__atomic_exchange_n(&j->seen[v], (uint8_t)1, __ATOMIC_RELAXED)) {
+            j->rc = 2;
+            j->where = k;
+            return NULL;
+        }
+    }
+    return NULL;
+}
+
 int oracle_verify_sa(const uint8_t *T, int64_t n, const int64_t *sa,
                      int nthreads, int64_t *where)
 {
     int64_t w = -1;
-    uint8_t *seen = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
-    if (!seen)
-        return -1;
-    for (int64_t k = 0; k < n; k++) {
-        int64_t v = sa[k];
-        if (v < 0 || v >= n) {
-            free(seen);
-            if (where)
-                *where = k;
-            return 1;
-        }
-        if (seen[v]) {
-            free(seen);
-            if (where)
-                *where = k;
-            return 2;
-        }
-        seen[v] = 1;
-    }
-    free(seen);
-    if (n < 2)
-        return 0;
     if (nthreads < 1)
         nthreads = 1;
+    if (nthreads > n)
+        nthreads = n > 0 ? (int)n : 1;
+    /* Permutation of [0, n): every value in range and none repeated. */
+    uint8_t *seen = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    struct perm_job *pj = (struct perm_job *)calloc((size_t)nthreads, sizeof *pj);
+    pthread_t *pth = (pthread_t *)calloc((size_t)nthreads, sizeof *pth);
+    if (!seen || !pj || !pth) {
+        free(seen);
+        free(pj);
+        free(pth);
+        return -1;
+    }
+    for (int t = 0; t < nthreads; t++) {
+        pj[t].sa = sa;
+        pj[t].n = n;
+        pj[t].a = n * t / nthreads;
+        pj[t].b = n * (t + 1) / nthreads;
+        pj[t].seen = seen;
+        pthread_create(&pth[t], NULL, perm_worker, &pj[t]);
+    }
+    int prc = 0;
+    for (int t = 0; t < nthreads; t++) {
+        pthread_join(pth[t], NULL);
+        if (pj[t].rc && (!prc || pj[t].rc < prc)) {
+            prc = pj[t].rc;
+            w = pj[t].where;
+        }
+    }
+    free(seen);
+    free(pj);
+    free(pth);
+    if (prc) {
+        if (where)
+            *where = w;
+        return prc;
+    }
+    if (n < 2)
+        return 0;
     int64_t pairs = n - 1;
     if (nthreads > pairs)
         nthreads = (int)pairs;
@@ -502,28 +546,33 @@ static int suffix_vs_string(const uint8_t *T, int64_t n, int64_t p, const uint8_
     return 0;
 }
 
-/* table[x] = the number of suffixes that sort before the k-base string whose
- * bases are the base-4 digits of x (A=0 C=1 G=2 T=3, most significant
- * first), for x in [0, 4^k); table[4^k] = n.  Each entry is the lower bound
- * of that string in the sorted suffixes (a binary search over sa). */
-void oracle_kmer_table(const uint8_t *T, int64_t n, const int64_t *sa, int k, int64_t *table)
+/* The number of suffixes that sort before the k-base string whose bases are
+ * the base-4 digits of x (A=0 C=1 G=2 T=3, most significant first), x in
+ * [0, 4^k): the lower bound of that string in the sorted suffixes, by binary
+ * search over sa. */
+int64_t oracle_kmer_rank(const uint8_t *T, int64_t n, const int64_t *sa, int k, int64_t x)
 {
     static const uint8_t letters[4] = {'A', 'C', 'G', 'T'};
     uint8_t X[32];
-    int64_t count = (int64_t)1 << (2 * k);
-    for (int64_t x = 0; x < count; x++) {
-        for (int t = 0; t < k; t++)
-            X[t] = letters[(x >> (2 * (k - 1 - t))) & 3];
-        int64_t lo = 0, hi = n; /* first rank whose suffix is not before X */
-        while (lo < hi) {
-            int64_t mid = lo + (hi - lo) / 2;
-            if (suffix_vs_string(T, n, sa[mid], X, k) < 0)
-                lo = mid + 1;
-            else
-                hi = mid;
-        }
-        table[x] = lo;
+    for (int t = 0; t < k; t++)
+        X[t] = letters[(x >> (2 * (k - 1 - t))) & 3];
+    int64_t lo = 0, hi = n; /* first rank whose suffix is not before X */
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (suffix_vs_string(T, n, sa[mid], X, k) < 0)
+            lo = mid + 1;
+        else
+            hi = mid;
     }
+    return lo;
+}
+
+/* table[x] = oracle_kmer_rank(x) for x in [0, 4^k); table[4^k] = n. */
+void oracle_kmer_table(const uint8_t *T, int64_t n, const int64_t *sa, int k, int64_t *table)
+{
+    int64_t count = (int64_t)1 << (2 * k);
+    for (int64_t x = 0; x < count; x++)
+        table[x] = oracle_kmer_rank(T, n, sa, k, x);
     table[count] = n;
 }
 
@@ -537,21 +586,22 @@ void oracle_kmer_table(const uint8_t *T, int64_t n, const int64_t *sa, int k, in
  * agrees on all 112 (m > 112, suffix >= 112 bases) also reads the 32-base
  * text windows from base 96 up to the one where it is decided.  *probes,
  * *windows count them; *table_reads is 1 or 0. */
-void oracle_probe_model_kmer(const uint8_t *T, int64_t n, const int64_t *sa, const int64_t *table, int k,
-                             int d0, const uint8_t *P, int64_t m, int64_t *probes, int64_t *windows,
-                             int64_t *table_reads, int64_t *lo_out, int64_t *hi_out)
+/* The same model for one query given its k-mer bracket: has_bracket says
+ * whether the query starts between ranks tlo - 1 and thi (tlo = table[x],
+ * thi = table[x + 1] for its first k bases x), else it starts at [-1, n) with
+ * its first d0 probes free. */
+void oracle_probe_model_bracket(const uint8_t *T, int64_t n, const int64_t *sa, int has_bracket, int64_t tlo,
+                                int64_t thi, int d0, const uint8_t *P, int64_t m, int64_t *probes,
+                                int64_t *windows, int64_t *table_reads, int64_t *lo_out, int64_t *hi_out)
 {
     *probes = 0;
     *windows = 0;
     *table_reads = 0;
     int64_t L = -1, R = n;
     int depth = 0, free_levels = 0;
-    if (table && m >= k && k > 0) {
-        int64_t x = 0;
-        for (int t = 0; t < k; t++)
-            x = x * 4 + (P[t] == 'A' ? 0 : P[t] == 'C' ? 1 : P[t] == 'G' ? 2 : 3);
-        L = table[x] - 1;
-        R = table[x + 1];
+    if (has_bracket) {
+        L = tlo - 1;
+        R = thi;
         *table_reads = 1;
     } else {
         free_levels = d0;
@@ -593,4 +643,17 @@ void oracle_probe_model_kmer(const uint8_t *T, int64_t n, const int64_t *sa, con
             L = M;
         }
     }
+}
+
+void oracle_probe_model_kmer(const uint8_t *T, int64_t n, const int64_t *sa, const int64_t *table, int k,
+                             int d0, const uint8_t *P, int64_t m, int64_t *probes, int64_t *windows,
+                             int64_t *table_reads, int64_t *lo_out, int64_t *hi_out)
+{
+    int has = table && m >= k && k > 0;
+    int64_t x = 0;
+    if (has)
+        for (int t = 0; t < k; t++)
+            x = x * 4 + (P[t] == 'A' ? 0 : P[t] == 'C' ? 1 : P[t] == 'G' ? 2 : 3);
+    oracle_probe_model_bracket(T, n, sa, has, has ? table[x] : 0, has ? table[x + 1] : 0, d0, P, m, probes,
+                               windows, table_reads, lo_out, hi_out);
 }

@@ -261,7 +261,7 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     uint64_t *tq = sc.get<uint64_t>(nwords + SA_TQ_PAD_WORDS);
     uint32_t *tv = sc.get<uint32_t>(nwords + SA_TQ_PAD_WORDS);
     uint4 *wrec = plain ? nullptr : sc.get<uint4>(4 * n_q);
-    int *flags = sc.get<int>(4);  // [0] pack error, [1] status, [2] worklist count
+    int *flags = sc.get<int>(4);  // [0] pack error, [1] status, [2] worklist count, [3] bad reference id
     unsigned long long *counter = sc.get<unsigned long long>(1);
     if (sc.failed) return SA_ERR_NOMEM;
     if (err != cudaSuccess) return status_from_cuda(err);
@@ -303,7 +303,11 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     L.chunk = params && params->chunk ? params->chunk : 64;
     L.front_probes = params && params->front_probes ? params->front_probes : default_front_probes(refs, n_refs);
     L.revcomp = params && (params->flags & SA_PARAM_REVERSE_COMPLEMENT);
+    L.expire_waits = params && (params->flags & SA_PARAM_EXPIRE_WAITS);
+    L.bad_ref = flags + 3;
     if (L.front_probes > 64) return SA_ERR_ARG;
+    int *dstatus = params ? params->device_status : nullptr;
+    if (dstatus && !on_device(dstatus)) return SA_ERR_ARG;
 
     if ((err = launch_pack_batch(L, tq, tv, s)) != cudaSuccess) return status_from_cuda(err);
     cudaEvent_t ev0 = params ? reinterpret_cast<cudaEvent_t>(params->search_events[0]) : nullptr;
@@ -317,8 +321,9 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     }
     if (err != cudaSuccess) return status_from_cuda(err);
     if (ev1 && (err = cudaEventRecord(ev1, s)) != cudaSuccess) return status_from_cuda(err);
+    if (dstatus && (err = launch_search_status(flags, dstatus, s)) != cudaSuccess) return status_from_cuda(err);
     if (!out_dev) {
-        int hflags[2] = {0, 0};
+        int hflags[4] = {0, 0, 0, 0};
         if ((err = cudaMemcpyAsync(out, out_d, n_q * sizeof(sa_result), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
             return status_from_cuda(err);
         if ((err = cudaMemcpyAsync(hflags, flags, sizeof hflags, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
@@ -326,8 +331,7 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
         if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return status_from_cuda(err);
         if (hflags[1]) return hflags[1];
         if (hflags[0]) return SA_ERR_BASE;
-        for (uint64_t i = 0; i < n_q; i++)
-            if (out[i].lo == ~0ull) return SA_ERR_ARG;
+        if (hflags[3]) return SA_ERR_ARG;
     }
     return SA_OK;
 }
@@ -529,7 +533,7 @@ namespace sa {
 
 int locate_impl(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_ref, const sa_result *res,
                 uint64_t n_q, uint32_t cap, uint64_t *out_offsets, void *out_pos, uint64_t out_pos_capacity,
-                void *stream) {
+                void *stream, int *dstatus = nullptr) {
     NvtxRange range("sa_locate");
     uint32_t width = 0;
     int st = check_refs(refs, n_refs, &width);
@@ -548,8 +552,10 @@ int locate_impl(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_
     if (!pos_dev && !out_pos_capacity) pos_d = nullptr;
     const uint64_t tiles = locate_tiles(n_q);
     uint64_t *partials = sc.get<uint64_t>(tiles + 1);
+    int *overflow = dstatus && pos_d ? sc.get<int>(1) : nullptr;
     if (sc.failed) return SA_ERR_NOMEM;
     if (err != cudaSuccess) return status_from_cuda(err);
+    if (overflow && (err = cudaMemsetAsync(overflow, 0, sizeof(int), s)) != cudaSuccess) return status_from_cuda(err);
     LocateLaunch L;
     memset(&L, 0, sizeof L);
     fill_ref_table(refs, n_refs, 0, &L.refs);
@@ -563,7 +569,9 @@ int locate_impl(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_
     L.out_pos = pos_d;
     L.capacity = pos_d ? out_pos_capacity : 0;
     L.partials = partials;
+    L.overflow = overflow;
     if ((err = launch_locate(L, s)) != cudaSuccess) return status_from_cuda(err);
+    if (overflow && (err = launch_capacity_status(overflow, dstatus, s)) != cudaSuccess) return status_from_cuda(err);
     if (!off_dev || !pos_dev) {
         uint64_t total = 0;
         if ((err = cudaMemcpyAsync(&total, off_d + n_q, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
@@ -577,6 +585,7 @@ int locate_impl(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_
             (err = cudaMemcpyAsync(out_pos, pos_d, kept * width, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
             return status_from_cuda(err);
         if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return status_from_cuda(err);
+        if (out_pos && total > out_pos_capacity) return SA_ERR_CAPACITY;
     }
     return SA_OK;
 }
@@ -598,7 +607,9 @@ int sa_search_locate(const sa_index *const *refs, uint32_t n_refs, const char *q
     const int st = search_impl(refs, n_refs, q_bases, q_offsets, q_ref, n_q, out, stream, params, false);
     if (st && st != SA_ERR_BASE && st != SA_ERR_ARG) return st;
     // invalid queries carry the all-ones result (no positions); the rest are located
-    const int lst = locate_impl(refs, n_refs, q_ref, out, n_q, cap, out_offsets, out_pos, out_pos_capacity, stream);
+    int *dstatus = params ? params->device_status : nullptr;
+    const int lst =
+        locate_impl(refs, n_refs, q_ref, out, n_q, cap, out_offsets, out_pos, out_pos_capacity, stream, dstatus);
     return lst ? lst : st;
 }
 

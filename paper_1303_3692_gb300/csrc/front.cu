@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t warp_first = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
     const uint64_t *__restrict__ tq = a.tq;
-    bool any_bad = false;
+    bool any_bad = false, any_bad_ref = false;
 
     // Offsets and reference of this lane's next query, read one query ahead.
     uint64_t nqa = 0, nqe = 0;
@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
             qa = t;
         }
         bool ok = range_ok && r < a.n_refs;
+        if (range_ok && r >= a.n_refs) any_bad_ref = true;
         const uint32_t m = ok ? (uint32_t)(qe - qa) : 0u;
 
         // First 128 bases and the validity of every base of the query.
@@ -267,6 +268,7 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
     }
     flush(staged);
     if (__any_sync(0xFFFFFFFFu, any_bad) && lane == 0) atomicOr(a.pack_err, 1);
+    if (__any_sync(0xFFFFFFFFu, any_bad_ref) && lane == 0) atomicOr(a.bad_ref, 1);
 }
 
 }  // namespace

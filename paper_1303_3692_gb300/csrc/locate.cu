@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_gather_kernel(const __gr
         for (uint64_t t = 0; t < kk; t++) {
             if (off + t < a.capacity) pos[off + t] = __ldg(sa + r.lo + t);
         }
+        if (a.overflow != nullptr && off + kk > a.capacity) atomicOr(a.overflow, 1);
     }
 }
 

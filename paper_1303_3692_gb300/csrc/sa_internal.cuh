@@ -310,12 +310,14 @@ struct SearchLaunch {
     uint32_t *wl_count;       // device: records in the worklist
     sa_result *out;
     int *pack_err;            // device flag: some query had a non-ACGT byte or bad offsets
+    int *bad_ref;             // device flag: some query named a reference id >= n_refs
     unsigned long long *counter;
     int *status;
     uint32_t smem_bytes;      // shared-memory key tables
     uint32_t threads, blocks, chunk;
     uint32_t front_probes;    // probes per query in the first pass
     bool revcomp;             // search every query's reverse complement (the batch is packed reversed)
+    bool expire_waits;        // test hook: the bounded key-table wait gives up at once
 };
 // Worklist record of a query the first pass did not finish (64 bytes):
 //   {L, R, m, q}            a bracket (L, R) holding both bounds (L = -1 is
@@ -326,6 +328,12 @@ cudaError_t launch_pack_batch(const SearchLaunch &L, uint64_t *tq, uint32_t *tv,
 cudaError_t launch_front(const SearchLaunch &L, cudaStream_t s);
 cudaError_t launch_search(const SearchLaunch &L, cudaStream_t s);
 cudaError_t launch_search_plain(const SearchLaunch &L, cudaStream_t s);
+// One thread: *dst = the call's status from its device flags (flags[1] a
+// wait that ran out, flags[0] a query that is not bases, flags[3] a bad
+// reference id), in that order of precedence.
+cudaError_t launch_search_status(const int *flags, int *dst, cudaStream_t s);
+// One thread: *dst = SA_ERR_CAPACITY when *overflow is set and *dst is SA_OK.
+cudaError_t launch_capacity_status(const int *overflow, int *dst, cudaStream_t s);
 uint32_t search_table_bytes(uint32_t depth);  // shared-memory bytes of a depth-d key table
 
 struct LocateLaunch {
@@ -339,6 +347,7 @@ struct LocateLaunch {
     void *out_pos;
     uint64_t capacity;
     uint64_t *partials;       // scratch: one entry per scan tile + 1
+    int *overflow;            // optional device flag: a position fell at or beyond capacity
 };
 uint64_t locate_tiles(uint64_t n_q);
 // Device address of the static scratch of sa_locate_noalloc on the current

@@ -82,8 +82,10 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Waits for the phase with the given parity, giving up after limit_ns.
+// Waits for the phase with the given parity, giving up after limit_ns (a
+// zero limit gives up at once without looking: the error-path test hook).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    if (limit_ns == 0) return false;
     const uint64_t t0 = global_ns();
     while (!mbar_try_wait(bar, parity)) {
         if (global_ns() - t0 > limit_ns) return false;
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(Occ<kOcc>::threads, Occ<kOcc>::blocks)
                           &mbar);
         }
     }
-    if (!mbar_wait_bounded(&mbar, 0, kWaitLimitNs)) {
+    if (!mbar_wait_bounded(&mbar, 0, a.expire_waits ? 0ull : kWaitLimitNs)) {
         if (tid == 0) atomicExch(a.status, SA_ERR_TIMEOUT);
         mbar_wait_bounded(&mbar, 0, kWaitLimitNs);  // let copies in flight land before the CTA exits
         return;
@@ -404,6 +406,7 @@ __global__ void __launch_bounds__(256) search_plain_kernel(const __grid_constant
     }
     if (bad || r >= a.n_refs) {
         if (bad) atomicOr(a.pack_err, 1);
+        if (!bad) atomicOr(a.bad_ref, 1);
         write_result(a.out, q, ~0ull, ~0ull);
         return;
     }
@@ -435,7 +438,28 @@ __global__ void __launch_bounds__(256) search_plain_kernel(const __grid_constant
     write_result(a.out, q, (uint64_t)LB, (uint64_t)(RB + 1));
 }
 
+__global__ void search_status_kernel(const int *flags, int *dst) {
+    int st = flags[1];
+    if (st == 0 && flags[0]) st = SA_ERR_BASE;
+    if (st == 0 && flags[3]) st = SA_ERR_ARG;
+    *dst = st;
+}
+
+__global__ void capacity_status_kernel(const int *overflow, int *dst) {
+    if (*overflow && *dst == SA_OK) *dst = SA_ERR_CAPACITY;
+}
+
 }  // namespace
+
+cudaError_t launch_search_status(const int *flags, int *dst, cudaStream_t s) {
+    search_status_kernel<<<1, 1, 0, s>>>(flags, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_capacity_status(const int *overflow, int *dst, cudaStream_t s) {
+    capacity_status_kernel<<<1, 1, 0, s>>>(overflow, dst);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_search(const SearchLaunch &L, cudaStream_t s) {
     if (L.n_q == 0) return cudaSuccess;

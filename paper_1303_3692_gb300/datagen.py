@@ -23,34 +23,73 @@ available; these recipes stand in for it:
 """
 from __future__ import annotations
 
+import concurrent.futures as _cf
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
 
 ASCII = np.frombuffer(b"ACGT", dtype=np.uint8)
 _CHUNK = 1 << 24
+_POOL = None
 
 
 def _rng(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(int(seed)))
 
 
+def _sub_rng(seed: int, tag: int, chunk: int) -> np.random.Generator:
+    """The generator of one chunk of one recipe step: a function of (seed,
+    step, chunk index) only, so the output does not depend on how many
+    threads draw the chunks."""
+    return np.random.Generator(np.random.PCG64(np.random.SeedSequence([int(seed), int(tag), int(chunk)])))
+
+
+def _map(fn, items):
+    """Runs fn over items on a thread pool (numpy's random fills, takes and
+    ufuncs release the GIL) and returns the results in order."""
+    global _POOL
+    items = list(items)
+    if len(items) <= 1:
+        return [fn(x) for x in items]
+    if _POOL is None:
+        _POOL = _cf.ThreadPoolExecutor(max(1, min(32, os.cpu_count() or 1)))
+    return list(_POOL.map(fn, items))
+
+
+def _seed_of(rng: np.random.Generator) -> int:
+    return int(rng.integers(0, 1 << 62))
+
+
 def background(rng: np.random.Generator, n: int, gc: float = 0.5) -> np.ndarray:
     """Codes 0..3 (A,C,G,T) drawn iid with the given GC content."""
     out = np.empty(n, dtype=np.uint8)
-    p = np.cumsum([(1 - gc) / 2, gc / 2, gc / 2])
-    for s in range(0, n, _CHUNK):
-        e = min(n, s + _CHUNK)
+    seed = _seed_of(rng)
+    t = np.cumsum([(1 - gc) / 2, gc / 2, gc / 2]).astype(np.float32)
+
+    def fill(c):
+        s, e = c * _CHUNK, min(n, (c + 1) * _CHUNK)
+        r = _sub_rng(seed, 1, c)
         if gc == 0.5:
-            out[s:e] = rng.integers(0, 4, e - s, dtype=np.uint8)
+            out[s:e] = r.integers(0, 4, e - s, dtype=np.uint8)
         else:
-            u = rng.random(e - s, dtype=np.float32)
-            out[s:e] = np.searchsorted(p.astype(np.float32), u, side="right").astype(np.uint8)
+            u = r.random(e - s, dtype=np.float32)
+            o = out[s:e]
+            np.greater_equal(u, t[0], out=o, casting="unsafe")
+            o += u >= t[1]
+            o += u >= t[2]
+
+    _map(fill, range((n + _CHUNK - 1) // _CHUNK))
     return out
 
 
-def _mutate(rng: np.random.Generator, block: np.ndarray, rate: float) -> None:
-    mask = rng.random(block.size) < rate
+def _mutate(rng: np.random.Generator, block: np.ndarray, rate) -> None:
+    """Independent substitutions: each base (with probability rate, a scalar
+    or one rate per row of a 2-D block) becomes one of the other three."""
+    r = np.asarray(rate, dtype=np.float64)
+    if block.ndim == 2 and r.ndim == 1:
+        r = r[:, None]
+    mask = rng.random(block.shape) < r
     k = int(mask.sum())
     if k:
         block[mask] = (block[mask] + rng.integers(1, 4, k, dtype=np.uint8)) & 3
@@ -91,24 +130,49 @@ def tandem_repeats(rng, codes: np.ndarray, cover: float,
 
 def repeat_families(rng, codes: np.ndarray, cover: float, unit_lens=(300, 6000),
                     n_fam: int = 4, div=(0.10, 0.20)) -> None:
+    """Copies of n_fam random consensus units per unit length, each copy with
+    its own divergence, written at random destinations (later copies
+    overwrite earlier ones) until each unit length covers cover/len(unit_lens)
+    of the text.  Copies are drawn in batches of independent chunks and
+    written in order."""
     n = codes.size
-    cons = {L: [rng.integers(0, 4, L, dtype=np.uint8) for _ in range(n_fam)] for L in unit_lens}
+    cons = {L: np.stack([rng.integers(0, 4, L, dtype=np.uint8) for _ in range(n_fam)]) for L in unit_lens}
     target = int(cover * n)
-    per_size = {L: target // len(unit_lens) for L in unit_lens}
-    for L in unit_lens:
-        done = 0
+    seed = _seed_of(rng)
+    for li, L in enumerate(unit_lens):
         if L >= n:
             continue
-        while done < per_size[L]:
-            block = cons[L][int(rng.integers(0, n_fam))].copy()
-            _mutate(rng, block, float(rng.uniform(div[0], div[1])))
-            dst = int(rng.integers(0, n - L + 1))
-            codes[dst:dst + L] = block
-            done += L
+        per = target // len(unit_lens)
+        copies = (per + L - 1) // L
+        batch = max(1, (1 << 22) // L)
+        chunks = [(c, c * batch, min(copies, (c + 1) * batch)) for c in range((copies + batch - 1) // batch)]
+
+        def draw(ch, L=L, li=li):
+            c, a, b = ch
+            r = _sub_rng(seed, 10 + li, c)
+            fam = r.integers(0, n_fam, b - a)
+            rate = r.uniform(div[0], div[1], b - a)
+            dst = r.integers(0, n - L + 1, b - a)
+            block = cons[L][fam]
+            _mutate(r, block, rate)
+            return dst, block
+
+        # draw a wave of chunks in parallel, write them in chunk order
+        wave = 64
+        for w0 in range(0, len(chunks), wave):
+            for dst, block in _map(draw, chunks[w0:w0 + wave]):
+                codes[dst[:, None] + np.arange(L)[None, :]] = block
 
 
 def to_ascii(codes: np.ndarray) -> np.ndarray:
-    return ASCII[codes]
+    out = np.empty(codes.size, dtype=np.uint8)
+
+    def conv(c):
+        s, e = c * _CHUNK, min(codes.size, (c + 1) * _CHUNK)
+        np.take(ASCII, codes[s:e], out=out[s:e])
+
+    _map(conv, range((codes.size + _CHUNK - 1) // _CHUNK))
+    return out
 
 
 def reference(n: int, seed: int, gc: float = 0.5, sd_cover: float = 0.0,
@@ -131,54 +195,64 @@ def queries(ref: np.ndarray, nq: int, seed: int, m=100, frac_sampled: float = 0.
 
     m is a fixed length or an inclusive (min, max) range drawn uniformly.
     Returns (bases uint8 ASCII concatenated, offsets int64 (nq+1), sampled bool).
+    Lengths and the sampled/random choice are drawn first; the bases of each
+    chunk of queries then come from that chunk's own generator.
     """
     rng = _rng(seed)
     n = ref.size
     if isinstance(m, (tuple, list)):
         lens = rng.integers(m[0], m[1] + 1, nq).astype(np.int64)
         mmax = int(m[1])
+        fixed = False
     else:
         lens = np.full(nq, int(m), dtype=np.int64)
         mmax = int(m)
+        fixed = True
     offsets = np.zeros(nq + 1, dtype=np.int64)
     np.cumsum(lens, out=offsets[1:])
     sampled = rng.random(nq) < frac_sampled
+    seed2 = _seed_of(rng)
     bases = np.empty(int(offsets[-1]), dtype=np.uint8)
     codes_of = np.full(256, 0, dtype=np.uint8)
     codes_of[ASCII] = np.arange(4, dtype=np.uint8)
-    step = max(1, (1 << 24) // max(1, mmax))
+    step = max(1, (1 << 22) // max(1, mmax))
     win = np.lib.stride_tricks.sliding_window_view(ref, mmax) if n >= mmax else None
-    for s in range(0, nq, step):
-        e = min(nq, s + step)
+
+    def chunk(c):
+        s, e = c * step, min(nq, (c + 1) * step)
+        r = _sub_rng(seed2, 2, c)
         k = e - s
         L = lens[s:e]
-        blk = rng.integers(0, 4, (k, mmax), dtype=np.uint8)
-        smp = sampled[s:e].copy()
+        blk = r.integers(0, 4, (k, mmax), dtype=np.uint8)
+        smp = sampled[s:e]
         if win is not None:
-            starts = (rng.random(k) * (n - L + 1)).astype(np.int64)
+            starts = (r.random(k) * (n - L + 1)).astype(np.int64)
             starts = np.minimum(starts, n - mmax)
             # sampled queries shorter than mmax near the end still start <= n-m
-            src = codes_of[win[starts[smp]]]
-            blk[smp] = src
-            nsub = rng.integers(subs[0], subs[1] + 1, k)
+            blk[smp] = np.take(codes_of, win[starts[smp]])
+            nsub = r.integers(subs[0], subs[1] + 1, k)
+            first = np.full(k, -1, dtype=np.int64)
             for j in range(int(subs[1])):
                 sel = smp & (nsub > j)
                 if not sel.any():
                     continue
                 rows = np.nonzero(sel)[0]
                 # distinct positions: draw position j among the L-j free slots
-                p = (rng.random(rows.size) * (L[rows] - j)).astype(np.int64)
+                p = (r.random(rows.size) * (L[rows] - j)).astype(np.int64)
                 if j == 1:
                     p = np.where(p >= first[rows], p + 1, p)
                 if j == 0:
-                    first = np.full(k, -1, dtype=np.int64)
                     first[rows] = p
-                blk[rows, p] = (blk[rows, p] + rng.integers(1, 4, rows.size, dtype=np.uint8)) & 3
+                blk[rows, p] = (blk[rows, p] + r.integers(1, 4, rows.size, dtype=np.uint8)) & 3
         else:
             smp[:] = False
-        sampled[s:e] = smp
-        mask = np.arange(mmax)[None, :] < L[:, None]
-        bases[offsets[s]:offsets[e]] = ASCII[blk[mask]]
+        if fixed:
+            np.take(ASCII, blk.reshape(-1), out=bases[offsets[s]:offsets[e]])
+        else:
+            mask = np.arange(mmax)[None, :] < L[:, None]
+            bases[offsets[s]:offsets[e]] = ASCII[blk[mask]]
+
+    _map(chunk, range((nq + step - 1) // step))
     return bases, offsets, sampled
 
 

@@ -37,6 +37,7 @@ SA_NO_KMER = 0x4
 SA_BUILD_HOST = 0x8
 SA_PARAM_Q_RANGE = 0x1
 SA_PARAM_REVERSE_COMPLEMENT = 0x2
+SA_PARAM_EXPIRE_WAITS = 0x4
 SA_LOCATE_NOALLOC_MAX_QUERIES = 1 << 26
 
 _u64 = ctypes.c_uint64
@@ -57,7 +58,7 @@ class sa_result(ctypes.Structure):
 class sa_search_params(ctypes.Structure):
     _fields_ = [("threads_per_block", _u32), ("blocks_per_sm", _u32), ("key_depth", _u32), ("chunk", _u32),
                 ("search_events", _vp * 2), ("flags", _u32), ("front_probes", _u32), ("q_first", _u64),
-                ("q_total", _u64), ("reserved", _u32 * 4)]
+                ("q_total", _u64), ("device_status", _vp), ("reserved", _u32 * 2)]
 
 
 # Every symbol include/sa.h declares, with its ctypes signature.
@@ -81,6 +82,7 @@ SIGNATURES = {
     "sa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sa_version": (_u32, []),
     "sa_random_read_rate": (ctypes.c_int, [_u64, _u32, _u32, ctypes.POINTER(ctypes.c_double), _vp]),
+    "sa_random_read_rate_ex": (ctypes.c_int, [_u64, _u32, _u32, _u32, ctypes.POINTER(ctypes.c_double), _vp]),
     "sa_suffix_array_host": (ctypes.c_int, [_vp, _u64, _u32, _vp]),
 }
 
@@ -315,11 +317,12 @@ def sa_search_locate(refs, q_bases, q_offsets, cap: int, q_ref=None, out=None, o
 
 
 def sa_random_read_rate(buffer_bytes: int = 4 << 30, threads_per_sm: int = 1024, steps: int = 64,
-                        stream=None) -> float:
-    """Dependent random 32-byte reads per second over a buffer far larger than L2."""
+                        stream=None, read_bytes: int = 32) -> float:
+    """Dependent random reads per second over a buffer far larger than L2; one
+    read is read_bytes contiguous bytes (32 .. 512)."""
     r = ctypes.c_double(0.0)
-    _check(lib().sa_random_read_rate(buffer_bytes, threads_per_sm, steps, ctypes.byref(r), _stream(stream)),
-           "sa_random_read_rate")
+    _check(lib().sa_random_read_rate_ex(buffer_bytes, threads_per_sm, steps, read_bytes, ctypes.byref(r),
+                                        _stream(stream)), "sa_random_read_rate_ex")
     return r.value
 
 

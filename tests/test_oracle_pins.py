@@ -255,3 +255,32 @@ def test_kmer_model_matches_search():
                 s = tab[x + 1] - tab[x]
                 assert tr == 1 and pr <= 2 * int(np.ceil(np.log2(s + 2)))
                 assert tab[x] - 1 <= lo <= hi <= tab[x + 1]
+
+
+def test_kmer_rank_and_bracket_model():
+    """One k-mer rank by binary search equals the brute-force count of the
+    suffixes below that k-string; the bracket form of the byte model, fed
+    those two ranks, is the table form (the form used where a 4^k table is
+    too large to build)."""
+    ref = datagen.reference(4000, 16, tandem_cover=0.1, family_cover=0.3)
+    text = bytes(ref).decode()
+    T = oracle.normalize(ref)
+    sa = oracle.sa_naive(T)
+    k = 4
+    tab = oracle.kmer_table(T, sa, k)
+    brute = _brute_kmer_table(text, k)
+    rng = np.random.default_rng(3)
+    for x in list(rng.integers(0, 4 ** k, 40)) + [0, 4 ** k - 1]:
+        assert oracle.kmer_rank(T, sa, k, int(x)) == brute[int(x)]
+    qb, qo, _ = datagen.queries(ref, 200, 17, m=(1, 130), frac_sampled=0.7, subs=(0, 1))
+    for q in range(200):
+        P = qb[qo[q]:qo[q + 1]]
+        want = oracle.probe_model_kmer(T, sa, tab, k, P, d0=5)
+        if P.size >= k:
+            x = oracle.kmer_code(P, k)
+            hi = oracle.kmer_rank(T, sa, k, x + 1) if x + 1 < 4 ** k else T.size
+            got = oracle.probe_model_bracket(T, sa, (oracle.kmer_rank(T, sa, k, x), hi), P, d0=5)
+        else:
+            got = oracle.probe_model_bracket(T, sa, None, P, d0=5)
+        assert got == want
+        assert got[3:] == oracle.search(T, sa, P)
