@@ -46,14 +46,13 @@ WORKLOAD = "repetitive-100Mbp-10M-q100-locate64"
 #       per-base validity masks written                         = 137.5
 #   search (front_kernel + search_kernel): 8 offset bytes + 25 packed query
 #       bytes + 12.5 validity bytes + one 64-byte k-mer entry + 32 per further
-#       record probe + 12 result bytes (lo, hi, count at the suffix array's
-#       width)                                                  = 134.7
-#   locate (3 kernels): 24 result bytes read + 8 offset bytes written + 4.1
-#       position bytes (suffix-array entry read and written)   = 36.1
+#       record probe + one 32-byte result                      = 154.7
+#   locate (3 kernels): 32 result bytes read + 8 offset bytes written + 4.1
+#       position bytes (suffix-array entry read and written)   = 44.1
 KERNEL_BYTES_PER_QUERY = {
     "pack_batch_kernel": 100 + 25 + 12.5,
-    "search": 8 + 25 + 12.5 + 64 + 32 * 0.41265 + 12,
-    "locate": 24 + 8 + 4.1072,
+    "search": 8 + 25 + 12.5 + 64 + 32 * 0.41265 + 32,
+    "locate": 32 + 8 + 4.1072,
 }
 # Random DRAM accesses per query of the search phase (the k-mer entry, further
 # record probes, text windows), from the same model: random 32- or 64-byte
@@ -189,7 +188,7 @@ def _time_count_steps(idxs, qb_d, qo_d, qr_d, params, args, local):
 
     dev = qb_d.device
     n_q = qo_d.numel() - 1
-    out = torch.empty((n_q, 3), dtype=torch.int64, device=dev)
+    out = torch.empty((n_q, sa.RESULT_FIELDS), dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream()
 
     def lib_event():
@@ -292,8 +291,8 @@ def run_paper_shaped(args, world, rank, local):
     n_max = w.q_offsets.size - 1
     qb_d, qo_d = torch.from_numpy(w.q_bases).to(dev), torch.from_numpy(w.q_offsets).to(dev)
     qb_h, qo_h = torch.from_numpy(w.q_bases).pin_memory(), torch.from_numpy(w.q_offsets).pin_memory()
-    out_d = torch.empty((n_max, 3), dtype=torch.int64, device=dev)
-    out_h = torch.empty((n_max, 3), dtype=torch.int64).pin_memory()
+    out_d = torch.empty((n_max, sa.RESULT_FIELDS), dtype=torch.int64, device=dev)
+    out_h = torch.empty((n_max, sa.RESULT_FIELDS), dtype=torch.int64).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     sizes = sorted({q for q in PAPER_TABLE5_SA if q <= n_max} | {n_max})
@@ -349,7 +348,7 @@ def run_paper_shaped(args, world, rank, local):
         "query_bases_per_s": value * m,
         "e2e": {"value": n_max / top["e2e_ms"] * 1e3, "unit": UNIT,
                 "h2d_bytes_per_step": int(w.q_offsets[n_max]) + (n_max + 1) * 8,
-                "d2h_bytes_per_step": n_max * 24, "ms_per_step": top["e2e_ms"]},
+                "d2h_bytes_per_step": n_max * 32, "ms_per_step": top["e2e_ms"]},
         "sweep": sweep, "build_s": build_s, "datagen_s": gen_s, "gpu_launches": args.steps * 3,
         "clocks": clk.summary(),
     }
@@ -422,7 +421,7 @@ def verified_suffix_array(idx, ref):
     return T, sa_h, dt
 
 
-def human_byte_model(T, sa_h, w, k: int, cap: int, sample: int = 20000, seed: int = 7):
+def human_byte_model(T, sa_h, w, k: int, cap: int, sample: int = 20000, seed: int = 7, kmer_order: bool = False):
     """Algorithmic bytes and random reads per query of each phase, from the
     oracle's byte model (oracle.probe_model_bracket: the lockstep search over
     each query's k-mer bracket, 32-byte records of 112 bases, text windows
@@ -455,15 +454,25 @@ def human_byte_model(T, sa_h, w, k: int, cap: int, sample: int = 20000, seed: in
     c = float(len(pick))
     per = {key: v / c for key, v in tot.items()}
     m = per["m"]
-    search = 8 + m / 4 + m / 8 + 64 * per["entry"] + 32 * per["further"] + 32 * per["windows"] + 24
+    probes = 64 * per["entry"] + 32 * per["further"] + 32 * per["windows"] + 32  # + the 32-byte result
+    if kmer_order:
+        # bucketing pass (offsets, packed bases and validity read, a 2-byte
+        # bucket id written), scatter pass (bucket id, offsets and packed
+        # bases read, a 64-byte record written), first pass reads the record
+        reorder = (8 + m / 4 + m / 8 + 2) + (2 + 8 + m / 4 + 64)
+        search = reorder + 64 + probes
+    else:
+        reorder = 0.0
+        search = 8 + m / 4 + m / 8 + probes
     return {
         "sample": int(c), "k": k,
         "bytes_per_query": {"pack_batch_kernel": m + m / 4 + m / 8, "search": search,
-                            "locate": 24 + 8 + 16 * per["kept"]},
+                            "locate": 32 + 8 + 16 * per["kept"]},
         # random sectors per query: 2 for the 64-byte entry, 1 per record, 1 per text window
         "random_sectors_per_query": 2 * per["entry"] + per["further"] + per["windows"],
         "entry_reads_per_query": per["entry"], "record_probes_per_query": per["further"],
         "text_windows_per_query": per["windows"], "mean_count": per["count"], "mean_kept": per["kept"],
+        "reorder_bytes_per_query": reorder, "order": "kmer" if kmer_order else "input",
         "source": "oracle.probe_model_bracket over the oracle-verified suffix array",
     }
 
@@ -519,7 +528,7 @@ def run_human_sized(args, world, rank, local):
 
     qb_d = torch.from_numpy(w.q_bases).to(dev)
     qo_d = torch.from_numpy(w.q_offsets).to(dev)
-    res = torch.empty((n_q, 3), dtype=torch.int64, device=dev)
+    res = torch.empty((n_q, sa.RESULT_FIELDS), dtype=torch.int64, device=dev)
     offs = torch.empty(n_q + 1, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -543,6 +552,9 @@ def run_human_sized(args, world, rank, local):
     del o
     pos = torch.empty(max(1, total_pos), dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    order = sa.sa_search_order(idx, n_q, p)
+    # pack, [bucket count, scan, scatter,] first pass, persistent pass, 3 locate kernels
+    launches = 1 + (3 if order == "kmer" else 0) + 2 + 3
 
     def timed(mode, steps, clk_needed=False):
         ts, ks, pk, lc = [], [], [], []
@@ -585,7 +597,7 @@ def run_human_sized(args, world, rank, local):
     # inside the timed region.
     qb_h = torch.from_numpy(w.q_bases).pin_memory()
     qo_h = torch.from_numpy(w.q_offsets).pin_memory()
-    res_h = torch.empty((n_q, 3), dtype=torch.int64).pin_memory()
+    res_h = torch.empty((n_q, sa.RESULT_FIELDS), dtype=torch.int64).pin_memory()
     offs_h = torch.empty(n_q + 1, dtype=torch.int64).pin_memory()
     pos_h = torch.empty(max(1, total_pos), dtype=torch.int64).pin_memory()
     del qb_d
@@ -637,7 +649,7 @@ def run_human_sized(args, world, rank, local):
     if rank == 0:
         peak, peak_kind = measured_peaks()
         T, sa_h, verify_s = verified_suffix_array(idx, w.ref)
-        model = human_byte_model(T, sa_h, w, idx.kmer_k, cap)
+        model = human_byte_model(T, sa_h, w, idx.kmer_k, cap, kmer_order=order == "kmer")
         phases = {"pack_batch_kernel": main["pack_ms"], "search": main["search_ms"], "locate": main["locate_ms"]}
         per_kernel = {}
         for name, ms in phases.items():
@@ -687,7 +699,8 @@ def run_human_sized(args, world, rank, local):
             "e2e": {"value": n_q / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_s * 1e3, "pinned_h2d_gbs": h2d_gbs,
                     "upload_bound_ms": h2d / (h2d_gbs * 1e9) * 1e3},
-            "gpu_launches": args.steps * 6,
+            "gpu_launches": args.steps * launches,
+            "search_order": order,
             "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clocks,
@@ -915,7 +928,7 @@ def run_ours(args, world, rank, local):
 
     qb_d = torch.from_numpy(w.q_bases).to(dev)
     qo_d = torch.from_numpy(w.q_offsets).to(dev)
-    res_d = torch.empty((n_q, 3), dtype=torch.int64, device=dev)
+    res_d = torch.empty((n_q, sa.RESULT_FIELDS), dtype=torch.int64, device=dev)
     offs_d = torch.empty(n_q + 1, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream()
     def lib_event():
@@ -982,7 +995,7 @@ def run_ours(args, world, rank, local):
     # End to end through the C ABI with host (pinned) buffers, copies inside.
     qb_h = torch.from_numpy(w.q_bases).pin_memory()
     qo_h = torch.from_numpy(w.q_offsets).pin_memory()
-    res_h = torch.empty((n_q, 3), dtype=torch.int64).pin_memory()
+    res_h = torch.empty((n_q, sa.RESULT_FIELDS), dtype=torch.int64).pin_memory()
     offs_h = torch.empty(n_q + 1, dtype=torch.int64).pin_memory()
     pos_h = torch.empty(max(1, total_pos), dtype=torch.int32).pin_memory()
 

@@ -70,18 +70,29 @@ extern "C" {
  * table, resident in device memory. */
 typedef struct sa_index sa_index;
 
-/* One query's result (Section IV: the SA interval of the query). */
+/* One query's result (Section IV: the SA interval of the query), 32 bytes:
+ * one aligned DRAM sector, so that a result written to a random slot is one
+ * whole-sector store. */
 typedef struct sa_result {
     uint64_t lo;    /* first suffix-array rank whose suffix has the query as prefix */
     uint64_t hi;    /* one past the last such rank (= RB + 1) */
     uint64_t count; /* hi - lo: occurrences of the query in the reference */
+    uint64_t flags; /* SA_RESULT_* bits */
 } sa_result;
+
+/* sa_result.flags: the query could not be searched (lo = hi = count = all-ones). */
+#define SA_RESULT_INVALID 0x1u
+/* sa_result.flags, set by sa_search_locate: count > cap, so only the first cap
+ * positions of the interval were located.  (sa_search_batch leaves it clear;
+ * after a separate sa_locate the condition is count > cap.) */
+#define SA_RESULT_TRUNCATED 0x2u
 
 /* Tuning knobs of the search kernel; zero fields take the defaults.
  * The results never depend on them. */
 typedef struct sa_search_params {
     uint32_t threads_per_block; /* 32..1024, multiple of 32 */
-    uint32_t blocks_per_sm;     /* persistent CTAs per SM */
+    uint32_t blocks_per_sm;     /* persistent CTAs per SM (at most 1024 threads per SM in all:
+                                   larger requests are reduced to that) */
     uint32_t key_depth;         /* shared-memory key-table depth d (<= the index's) */
     uint32_t chunk;             /* queries a warp takes from the global counter at once */
     void *search_events[2];     /* optional cudaEvent_t pair, recorded on the stream right
@@ -134,6 +145,19 @@ typedef struct sa_search_params {
  * before it exits).  The call then reports SA_ERR_TIMEOUT and the results of
  * the queries that kernel was to finish are undefined. */
 #define SA_PARAM_EXPIRE_WAITS 0x4u
+/* sa_search_params.flags: the order in which the batch's queries are
+ * searched (the results do not depend on it).  By default a call whose
+ * indexes take more than 48 GB of device memory searches in k-mer order: the
+ * queries are first bucketed by their first k bases, so that the random
+ * reads in flight stay within a narrow slice of the index (random reads over
+ * a wider footprint than the GPU's address translation covers run up to five
+ * times slower); smaller indexes are searched in input order, the queries a
+ * k-mer entry settles finishing in a one-thread-per-query first pass.  These
+ * flags force one order (setting both is SA_ERR_ARG).  The default takes
+ * k-mer order only for batches of at least 2^20 queries: a smaller batch is
+ * in flight all at once whatever its order. */
+#define SA_PARAM_KMER_ORDER 0x8u
+#define SA_PARAM_INPUT_ORDER 0x10u
 
 /*
  * sa_build -- index one reference (Section III).
@@ -186,7 +210,8 @@ int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_inde
  *             unless sa_search_batch_ex is given SA_PARAM_Q_RANGE).
  *  q_ref      n_q reference ids (< n_refs), or NULL when n_refs == 1.
  *  n_q        number of queries, < 2^32 (0 is allowed and does nothing).
- *  out        n_q results (host or device).
+ *  out        n_q results (host or device; in device memory 32-byte aligned,
+ *             since each result is stored as one 32-byte sector).
  *  stream     CUDA stream or NULL.
  *
  * The work runs as three kernels on the stream: the batch's bases are packed
@@ -200,7 +225,8 @@ int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_inde
  *
  * A query that cannot be searched -- a byte outside {A,C,G,T,a,c,g,t}, an
  * out-of-range q_ref, or offsets inconsistent with the batch's range -- gets
- * lo = hi = count = UINT64_MAX; the other queries are unaffected.  When the
+ * lo = hi = count = UINT64_MAX and flags = SA_RESULT_INVALID; the other
+ * queries are unaffected.  When the
  * output is in host memory the call also reports it: SA_ERR_BASE for a byte
  * or range problem, else SA_ERR_ARG for a reference id.
  *
@@ -217,9 +243,10 @@ int sa_search_batch_ex(const sa_index *const *refs, uint32_t n_refs, const char 
 
 /*
  * sa_search_batch_plain -- same contract and results as sa_search_batch, by
- * the direct GPU rendering of Alg. 1: one thread per query, two independent
- * full binary searches (LB, then RB) over [-1, n), bases compared one at a
- * time.  It is the comparison point for the optimized kernel.
+ * the paper's direct scheme (Section IV, Alg. 1): one thread per query, two
+ * independent binary searches over the whole suffix array (the lower bound
+ * LB, then the upper bound RB + 1), bases compared one at a time.  It is the
+ * comparison point for the optimized kernel.
  */
 int sa_search_batch_plain(const sa_index *const *refs, uint32_t n_refs, const char *q_bases,
                           const uint64_t *q_offsets, const uint32_t *q_ref, uint64_t n_q,
@@ -297,7 +324,10 @@ int sa_search_locate(const sa_index *const *refs, uint32_t n_refs, const char *q
  *
  * The first call on a device looks up the array's device address for that
  * device (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  All calls share the one array and it keeps the last call's
+ * stream capture.  Later calls check that the cached address is still device
+ * memory of that device (one cudaPointerGetAttributes) and look it up again
+ * if not: after cudaDeviceReset the module, and so the array, may move.  (A
+ * reset also frees every index built before it.)  All calls share the one array and it keeps the last call's
  * contents (no call needs it to start at zero: every partial sum a call reads
  * is written earlier in the same call), so calls that overlap on the GPU race:
  * run them on one stream or order them with events.
@@ -308,6 +338,20 @@ int sa_search_locate(const sa_index *const *refs, uint32_t n_refs, const char *q
 int sa_locate_noalloc(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_ref,
                       const sa_result *res, uint64_t n_q, uint32_t cap, uint64_t *out_offsets,
                       void *out_pos, uint64_t out_pos_capacity, void *stream);
+
+/* Whether sa_search_batch_ex (or sa_search_locate) of n_q queries over these
+ * indexes with these params (may be NULL) would search in k-mer order:
+ * *kmer_order = 1, else 0 (see SA_PARAM_KMER_ORDER).  Errors: SA_ERR_ARG. */
+int sa_search_order(const sa_index *const *refs, uint32_t n_refs, uint64_t n_q, const sa_search_params *params,
+                    int *kmer_order);
+
+/* Facts of the library's scratch pool on the current device: the bytes it
+ * holds (reserved), the bytes allocated from it now (used) and the most ever
+ * allocated at once since the last reset (used_high); reset_high != 0 then
+ * resets that high-water mark.  Any output pointer may be NULL.  Lets a caller
+ * see what scratch the library keeps, and check that a call allocated none.
+ * Errors: SA_ERR_CUDA. */
+int sa_scratch_info(uint64_t *reserved_bytes, uint64_t *used_bytes, uint64_t *used_high_bytes, int reset_high);
 
 /* Writes the index (header, packed text, suffix array, key table and a
  * 64-bit FNV-1a checksum) to path.  Synchronous.  SA_ERR_IO on failure. */

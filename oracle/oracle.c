@@ -15,9 +15,10 @@
  * Every routine states the passage it follows.  Readings taken where the paper
  * is silent or garbled:
  *   R1  Alg. 1's bound tests are read as the standard lower/upper bound:
- *       LB loop moves R to the pivot when P <= m-prefix(pivot suffix),
- *       RB loop moves R to the pivot when P <  m-prefix(pivot suffix).
- *   R2  The initial boundaries are L = -1, R = n (exclusive sentinels).
+ *       LB is the first rank with P <= m-prefix(suffix), and RB + 1 the
+ *       first rank with P < m-prefix(suffix).
+ *   R2  The search covers every rank: Alg. 1's boundaries -1 and n are the
+ *       exclusive ends of the range [0, n).
  *   R3  No terminator is printed; Table I orders a proper prefix before any
  *       longer suffix that starts with it, so a suffix that ends before the
  *       query does compares smaller than the query.
@@ -268,35 +269,34 @@ static int query_cmp(const uint8_t *T, int64_t n, int64_t p,
     return 0;
 }
 
-/* Alg. 1 (cudaGeneBinSearch) for one query, run on the CPU: two binary
- * searches over the suffix array with boundaries L = -1, R = n (R2).  The
- * first finds LB (R moves when P <= pivot's m-prefix, R1) and LB = R; the
- * second finds RB (R moves when P < pivot's m-prefix) and RB = L.  Results
- * are half-open (R4): lo = LB, hi = RB + 1. */
+/* The interval of Section IV for one query, by two binary searches over the
+ * suffix array -- the search Alg. 1 performs on the GPU, written here as the
+ * textbook lower and upper bound over the half-open range of ranks [0, n)
+ * (R2: every rank can be an answer).  lo is the first rank whose suffix's
+ * m-prefix does not sort before P (R1, R3); hi is the first rank whose
+ * suffix's m-prefix sorts after P.  Every rank in [lo, hi) has P as a prefix
+ * (R4); a miss gives lo = hi (R5). */
 void oracle_search(const uint8_t *T, int64_t n, const int64_t *sa,
                    const uint8_t *P, int64_t m, int64_t *lo, int64_t *hi)
 {
-    int64_t L = -1, R = n;
-    while (R > L + 1) {
-        int64_t pivot = (L + R) >> 1;
-        if (query_cmp(T, n, sa[pivot], P, m, NULL) <= 0)
-            R = pivot;
+    int64_t a = 0, b = n; /* the lower bound lies in [a, b] */
+    while (a < b) {
+        int64_t mid = a + (b - a) / 2;
+        if (query_cmp(T, n, sa[mid], P, m, NULL) > 0) /* S_SA[mid] sorts before P */
+            a = mid + 1;
         else
-            L = pivot;
+            b = mid;
     }
-    int64_t LB = R;
-    L = -1;
-    R = n;
-    while (R > L + 1) {
-        int64_t pivot = (L + R) >> 1;
-        if (query_cmp(T, n, sa[pivot], P, m, NULL) < 0)
-            R = pivot;
+    *lo = a;
+    b = n; /* the upper bound lies in [lo, n] */
+    while (a < b) {
+        int64_t mid = a + (b - a) / 2;
+        if (query_cmp(T, n, sa[mid], P, m, NULL) >= 0) /* S_SA[mid] does not sort after P */
+            a = mid + 1;
         else
-            L = pivot;
+            b = mid;
     }
-    int64_t RB = L;
-    *lo = LB;
-    *hi = RB + 1;
+    *hi = a;
 }
 
 /* The interval by its definition, without a suffix array: lo is the number

@@ -20,10 +20,13 @@ import numpy as np
 
 from . import sa
 
-# (threads per block, blocks per SM, key-table depth, chunk, first-pass probes)
+# (threads per block, blocks per SM, key-table depth, chunk, first-pass probes).
+# Every shape keeps 1024 threads per SM: the persistent kernel takes 64
+# registers a thread, so more resident threads cannot fit (the library
+# reduces such requests) and shapes that forced fewer registers spilled.
 DEFAULT_CANDIDATES: Tuple[Tuple[int, ...], ...] = (
     (1024, 1, 13, 64, 3), (1024, 1, 13, 64, 1), (1024, 1, 13, 64, 2), (1024, 1, 13, 64, 4),
-    (1024, 1, 12, 64, 3), (1024, 1, 13, 32, 3), (512, 2, 12, 64, 3), (256, 6, 10, 64, 3),
+    (1024, 1, 12, 64, 3), (1024, 1, 13, 32, 3), (512, 2, 12, 64, 3), (256, 4, 11, 64, 3),
 )
 
 LENGTH_BUCKETS = (64, 128, 192, 300, 1 << 62)
@@ -112,7 +115,7 @@ def autotune(refs, q_bases, q_offsets, q_ref=None, sample: int = 1_000_000,
     first = int(qo[0].item())
     total = int((qo[-1] - qo[0]).item())
     qr = None if q_ref is None else q_ref[:n_q]
-    out = torch.empty((n_q, 3), dtype=torch.int64, device=q_offsets.device)
+    out = torch.empty((n_q, sa.RESULT_FIELDS), dtype=torch.int64, device=q_offsets.device)
     ref_result = None
     timings: List[Tuple[Tuple[int, ...], float]] = []
     for cand in candidates:

@@ -159,6 +159,28 @@ uint32_t default_front_probes(const sa_index *const *refs, uint32_t n_refs) {
 }
 constexpr uint32_t kSmemBudget = 200 * 1024;
 
+// Indexes of more device bytes than this (in one call) are searched in k-mer
+// order: the random reads of a search over a larger footprint outrun the
+// GPU's address-translation reach (measured on the GB300: 34-38 G random
+// sectors/s up to 64 GB, 22 G/s at 80 GB, 8 G/s at 190 GB; 40 G/s when the
+// reads in flight stay within a 1 GB slice of a 192 GB buffer).
+// The order only narrows the reads in flight when the batch is much larger
+// than the ~150,000 lanes the kernels keep busy at once.
+constexpr uint64_t kKmerOrderMinBytes = 48ull << 30;
+constexpr uint64_t kKmerOrderMinQueries = 1ull << 20;
+
+// Whether a search of n_q queries over these indexes runs in k-mer order
+// (order: the SA_PARAM_*_ORDER flags of the call).
+bool use_kmer_order(const sa_index *const *refs, uint32_t n_refs, uint64_t n_q, uint32_t order) {
+    uint64_t ktotal = 0, index_bytes = 0;
+    for (uint32_t r = 0; r < n_refs; r++) {
+        if (refs[r]->krt) ktotal += 1ull << (2 * refs[r]->kmer_k);
+        index_bytes += refs[r]->device_bytes;
+    }
+    if (ktotal == 0 || order == SA_PARAM_INPUT_ORDER) return false;
+    return order == SA_PARAM_KMER_ORDER || (index_bytes > kKmerOrderMinBytes && n_q >= kKmerOrderMinQueries);
+}
+
 int check_refs(const sa_index *const *refs, uint32_t n_refs, uint32_t *width) {
     if (!refs || n_refs == 0 || n_refs > SA_MAX_REFS) return SA_ERR_ARG;
     int dev = 0;
@@ -189,9 +211,12 @@ uint32_t fill_ref_table(const sa_index *const *refs, uint32_t n_refs, uint32_t w
         use[deepest]--;
     }
     uint32_t off = 0;
+    uint64_t kbase = 0;
     for (uint32_t r = 0; r < n_refs; r++) {
         const sa_index *x = refs[r];
         RefDesc &d = t->r[r];
+        d.kbase = kbase;
+        if (x->krt) kbase += 1ull << (2 * x->kmer_k);
         d.text = x->text;
         d.sa = x->sa;
         d.keys = x->keys;
@@ -208,9 +233,118 @@ uint32_t fill_ref_table(const sa_index *const *refs, uint32_t n_refs, uint32_t w
     return off;
 }
 
+// The search of a batch whose inputs are in device memory: ascii holds the
+// batch's bases from offset `first` on (query q is ascii[q_off[q] - first ..
+// q_off[q + 1] - first)), q_off and q_ref are device arrays and out device
+// results.  Scratch comes from sc, on stream s.  *flags_out receives the
+// call's device flags ([0] a byte that is not a base, [1] a wait that ran
+// out, [3] a bad reference id).
+int search_device(const sa_index *const *refs, uint32_t n_refs, uint32_t width, const char *ascii,
+                  const uint64_t *q_off, const uint32_t *q_ref, uint64_t n_q, uint64_t first, uint64_t total,
+                  sa_result *out, cudaStream_t s, const sa_search_params *params, bool plain, uint32_t trunc_cap,
+                  Scratch &sc, int **flags_out) {
+    const uint32_t order = params ? params->flags & (SA_PARAM_KMER_ORDER | SA_PARAM_INPUT_ORDER) : 0u;
+    if (order == (SA_PARAM_KMER_ORDER | SA_PARAM_INPUT_ORDER)) return SA_ERR_ARG;
+    const uint32_t threads = params && params->threads_per_block ? params->threads_per_block : 1024;
+    uint32_t bps = params && params->blocks_per_sm ? params->blocks_per_sm : 1;
+    if (threads < 32 || threads > 1024 || threads % 32 || bps == 0 || threads * bps > 2048) return SA_ERR_ARG;
+    if (threads * bps > 1024) bps = 1024 / threads;  // the persistent kernel takes 64 registers a thread
+    if (params && params->front_probes > 64) return SA_ERR_ARG;
+    cudaError_t err = cudaSuccess;
+    const uint64_t nwords = (total + 31) / 32;
+    uint64_t *tq = sc.get<uint64_t>(nwords + SA_TQ_PAD_WORDS);
+    uint32_t *tv = sc.get<uint32_t>(nwords + SA_TQ_PAD_WORDS);
+    uint4 *wrec = plain ? nullptr : sc.get<uint4>(4 * n_q);
+    uint64_t ktotal = 0;
+    for (uint32_t r = 0; r < n_refs; r++)
+        if (refs[r]->krt) ktotal += 1ull << (2 * refs[r]->kmer_k);
+    const bool kmer_order = !plain && use_kmer_order(refs, n_refs, n_q, order);
+    uint16_t *qbucket = kmer_order ? sc.get<uint16_t>(n_q) : nullptr;
+    uint4 *wrec_in = kmer_order ? sc.get<uint4>(4 * n_q) : nullptr;
+    uint32_t *bh = kmer_order ? sc.get<uint32_t>(2 * (kNumBuckets + 1)) : nullptr;
+    // [0] pack error, [1] status, [2] worklist count, [3] bad reference id,
+    // [4] records of the k-mer-ordered list
+    int *flags = sc.get<int>(8);
+    unsigned long long *counter = sc.get<unsigned long long>(1);
+    if (sc.failed) return SA_ERR_NOMEM;
+    if (((uintptr_t)wrec & 31u) != 0) return SA_ERR_CUDA;  // the search reads 32-byte records
+    if ((err = cudaMemsetAsync(flags, 0, 8 * sizeof(int), s)) != cudaSuccess) return status_from_cuda(err);
+    if ((err = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s)) != cudaSuccess)
+        return status_from_cuda(err);
+    if (bh && (err = cudaMemsetAsync(bh, 0, (kNumBuckets + 1) * sizeof(uint32_t), s)) != cudaSuccess)
+        return status_from_cuda(err);
+    *flags_out = flags;
+
+    SearchLaunch L;
+    memset(&L, 0, sizeof L);
+    // shared memory per SM is 228 KB; each CTA also holds ~4 KB of descriptors
+    const uint32_t per_cta = 224u * 1024u / bps - 6144u;
+    const uint32_t budget = per_cta < kSmemBudget ? per_cta : kSmemBudget;
+    const uint32_t want_depth = params && params->key_depth ? params->key_depth : kDefaultDepth;
+    L.smem_bytes = fill_ref_table(refs, n_refs, plain ? 0 : want_depth, &L.refs, budget);
+    L.n_refs = n_refs;
+    L.width = width;
+    L.ascii = ascii;
+    L.tq = tq;
+    L.tv = tv;
+    L.nwords = nwords;
+    L.q_off = q_off;
+    L.first = first;
+    L.total = total;
+    L.q_ref = q_ref;
+    L.n_q = n_q;
+    L.wrec = wrec;
+    L.wl_count = reinterpret_cast<uint32_t *>(flags + 2);
+    L.out = out;
+    L.pack_err = flags;
+    L.counter = counter;
+    L.status = flags + 1;
+    const int sms = device_sm_count();
+    L.threads = threads;
+    L.blocks = (uint32_t)sms * bps;
+    L.chunk = params && params->chunk ? params->chunk : 64;
+    // with the queries in k-mer order neighbouring lanes share pages and rows,
+    // and the first pass does best with three probes (measured)
+    L.front_probes = params && params->front_probes ? params->front_probes
+                                                    : (kmer_order ? 3u : default_front_probes(refs, n_refs));
+    L.revcomp = params && (params->flags & SA_PARAM_REVERSE_COMPLEMENT);
+    L.expire_waits = params && (params->flags & SA_PARAM_EXPIRE_WAITS);
+    L.trunc_cap = trunc_cap;
+    L.ktotal = ktotal;
+    L.qbucket = qbucket;
+    L.bhist = bh;
+    L.bcursor = bh ? bh + kNumBuckets + 1 : nullptr;
+    L.wrec_in = wrec_in;
+    L.wl_in_count = reinterpret_cast<uint32_t *>(flags + 4);
+    L.bad_ref = flags + 3;
+
+    if ((err = launch_pack_batch(L, tq, tv, s)) != cudaSuccess) return status_from_cuda(err);
+    cudaEvent_t ev0 = params ? reinterpret_cast<cudaEvent_t>(params->search_events[0]) : nullptr;
+    cudaEvent_t ev1 = params ? reinterpret_cast<cudaEvent_t>(params->search_events[1]) : nullptr;
+    if (ev0 && (err = cudaEventRecord(ev0, s)) != cudaSuccess) return status_from_cuda(err);
+    if (plain) {
+        err = launch_search_plain(L, s);
+    } else {
+        if (kmer_order) err = launch_bucketed_worklist(L, wrec_in, s);
+        if (err == cudaSuccess) err = launch_front(L, s);
+        if (err == cudaSuccess) err = launch_search(L, s);
+    }
+    if (err != cudaSuccess) return status_from_cuda(err);
+    if (ev1 && (err = cudaEventRecord(ev1, s)) != cudaSuccess) return status_from_cuda(err);
+    return SA_OK;
+}
+
+// The call's status from its device flags read back to the host.
+int host_status(const int hflags[4]) {
+    if (hflags[1]) return hflags[1];
+    if (hflags[0]) return SA_ERR_BASE;
+    if (hflags[3]) return SA_ERR_ARG;
+    return SA_OK;
+}
+
 int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_bases, const uint64_t *q_offsets,
                 const uint32_t *q_ref, uint64_t n_q, sa_result *out, void *stream, const sa_search_params *params,
-                bool plain) {
+                bool plain, uint32_t trunc_cap = ~0u) {
     NvtxRange range(plain ? "sa_search_plain" : "sa_search");
     uint32_t width = 0;
     int st = check_refs(refs, n_refs, &width);
@@ -239,6 +373,10 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     if (last < first) return SA_ERR_ARG;
     const uint64_t total = last - first;
     if (total > 0 && !q_bases) return SA_ERR_ARG;
+    const bool out_dev = on_device(out);
+    if (out_dev && ((uintptr_t)out & 31u)) return SA_ERR_ARG;  // results are stored as whole 32-byte sectors
+    int *dstatus = params ? params->device_status : nullptr;
+    if (dstatus && !on_device(dstatus)) return SA_ERR_ARG;
 
     Scratch sc{s};
     cudaError_t err = cudaSuccess;
@@ -255,72 +393,13 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     }
     const uint64_t *off_d = device_view(q_offsets, n_q + 1, sc, &err);
     const uint32_t *ref_d = n_refs > 1 || q_ref ? device_view(q_ref, n_q, sc, &err) : nullptr;
-    const bool out_dev = on_device(out);
     sa_result *out_d = out_dev ? out : sc.get<sa_result>(n_q);
-    const uint64_t nwords = (total + 31) / 32;
-    uint64_t *tq = sc.get<uint64_t>(nwords + SA_TQ_PAD_WORDS);
-    uint32_t *tv = sc.get<uint32_t>(nwords + SA_TQ_PAD_WORDS);
-    uint4 *wrec = plain ? nullptr : sc.get<uint4>(4 * n_q);
-    int *flags = sc.get<int>(4);  // [0] pack error, [1] status, [2] worklist count, [3] bad reference id
-    unsigned long long *counter = sc.get<unsigned long long>(1);
     if (sc.failed) return SA_ERR_NOMEM;
     if (err != cudaSuccess) return status_from_cuda(err);
-    if (((uintptr_t)wrec & 31u) != 0) return SA_ERR_CUDA;  // the search reads 32-byte records
-    if ((err = cudaMemsetAsync(flags, 0, 4 * sizeof(int), s)) != cudaSuccess) return status_from_cuda(err);
-    if ((err = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s)) != cudaSuccess)
-        return status_from_cuda(err);
-
-    SearchLaunch L;
-    memset(&L, 0, sizeof L);
-    const uint32_t threads = params && params->threads_per_block ? params->threads_per_block : 1024;
-    const uint32_t bps = params && params->blocks_per_sm ? params->blocks_per_sm : 1;
-    if (threads < 32 || threads > 1024 || threads % 32 || bps == 0 || threads * bps > 2048) return SA_ERR_ARG;
-    // shared memory per SM is 228 KB; each CTA also holds ~4 KB of descriptors
-    const uint32_t per_cta = 224u * 1024u / bps - 6144u;
-    const uint32_t budget = per_cta < kSmemBudget ? per_cta : kSmemBudget;
-    const uint32_t want_depth = params && params->key_depth ? params->key_depth : kDefaultDepth;
-    L.smem_bytes = fill_ref_table(refs, n_refs, plain ? 0 : want_depth, &L.refs, budget);
-    L.n_refs = n_refs;
-    L.width = width;
-    L.ascii = bases_d;
-    L.tq = tq;
-    L.tv = tv;
-    L.nwords = nwords;
-    L.q_off = off_d;
-    L.first = first;
-    L.total = total;
-    L.q_ref = ref_d;
-    L.n_q = n_q;
-    L.wrec = wrec;
-    L.wl_count = reinterpret_cast<uint32_t *>(flags + 2);
-    L.out = out_d;
-    L.pack_err = flags;
-    L.counter = counter;
-    L.status = flags + 1;
-    const int sms = device_sm_count();
-    L.threads = threads;
-    L.blocks = (uint32_t)sms * bps;
-    L.chunk = params && params->chunk ? params->chunk : 64;
-    L.front_probes = params && params->front_probes ? params->front_probes : default_front_probes(refs, n_refs);
-    L.revcomp = params && (params->flags & SA_PARAM_REVERSE_COMPLEMENT);
-    L.expire_waits = params && (params->flags & SA_PARAM_EXPIRE_WAITS);
-    L.bad_ref = flags + 3;
-    if (L.front_probes > 64) return SA_ERR_ARG;
-    int *dstatus = params ? params->device_status : nullptr;
-    if (dstatus && !on_device(dstatus)) return SA_ERR_ARG;
-
-    if ((err = launch_pack_batch(L, tq, tv, s)) != cudaSuccess) return status_from_cuda(err);
-    cudaEvent_t ev0 = params ? reinterpret_cast<cudaEvent_t>(params->search_events[0]) : nullptr;
-    cudaEvent_t ev1 = params ? reinterpret_cast<cudaEvent_t>(params->search_events[1]) : nullptr;
-    if (ev0 && (err = cudaEventRecord(ev0, s)) != cudaSuccess) return status_from_cuda(err);
-    if (plain) {
-        err = launch_search_plain(L, s);
-    } else {
-        err = launch_front(L, s);
-        if (err == cudaSuccess) err = launch_search(L, s);
-    }
-    if (err != cudaSuccess) return status_from_cuda(err);
-    if (ev1 && (err = cudaEventRecord(ev1, s)) != cudaSuccess) return status_from_cuda(err);
+    int *flags = nullptr;
+    st = search_device(refs, n_refs, width, bases_d, off_d, ref_d, n_q, first, total, out_d, s, params, plain,
+                       trunc_cap, sc, &flags);
+    if (st) return st;
     if (dstatus && (err = launch_search_status(flags, dstatus, s)) != cudaSuccess) return status_from_cuda(err);
     if (!out_dev) {
         int hflags[4] = {0, 0, 0, 0};
@@ -329,9 +408,7 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
         if ((err = cudaMemcpyAsync(hflags, flags, sizeof hflags, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
             return status_from_cuda(err);
         if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return status_from_cuda(err);
-        if (hflags[1]) return hflags[1];
-        if (hflags[0]) return SA_ERR_BASE;
-        if (hflags[3]) return SA_ERR_ARG;
+        return host_status(hflags);
     }
     return SA_OK;
 }
@@ -416,6 +493,18 @@ struct FileHeader {
 const char kMagic[8] = {'S', 'A', 'G', 'B', '3', '0', '0', '\0'};
 
 }  // namespace
+}  // namespace sa
+
+namespace sa {
+// Host batches of at least this many queries (bases and offsets in host
+// memory) run in chunks on two library streams: each chunk's upload overlaps
+// the previous chunk's kernels and the one before's downloads, instead of one
+// upload of the whole batch, then the kernels, then the downloads.
+constexpr uint64_t kPipelineMinQueries = 1ull << 21;
+int search_pipelined(const sa_index *const *refs, uint32_t n_refs, uint32_t width, const char *q_bases,
+                     const uint64_t *q_offsets, const uint32_t *q_ref, uint64_t n_q, sa_result *out,
+                     cudaStream_t s, const sa_search_params *params, bool locate, uint32_t cap,
+                     uint64_t *out_offsets, void *out_pos, uint64_t capacity);
 }  // namespace sa
 
 using namespace sa;
@@ -512,14 +601,46 @@ int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_inde
     return SA_OK;
 }
 
+}  // extern "C"
+
+namespace sa {
+// Whether a call takes the chunked host path: bases and offsets in host
+// memory and a large batch.
+bool pipelined(const char *q_bases, const uint64_t *q_offsets, uint64_t n_q) {
+    return n_q >= kPipelineMinQueries && q_offsets && !on_device(q_offsets) && (!q_bases || !on_device(q_bases));
+}
+
+int search_pipelined_entry(const sa_index *const *refs, uint32_t n_refs, const char *q_bases,
+                           const uint64_t *q_offsets, const uint32_t *q_ref, uint64_t n_q, sa_result *out,
+                           void *stream, const sa_search_params *params, bool locate, uint32_t cap,
+                           uint64_t *out_offsets, void *out_pos, uint64_t capacity) {
+    NvtxRange range(locate ? "sa_search_locate" : "sa_search");
+    uint32_t width = 0;
+    int st = check_refs(refs, n_refs, &width);
+    if (st) return st;
+    if (!out || (n_refs > 1 && !q_ref) || n_q >= (1ull << 32) || (locate && !out_offsets)) return SA_ERR_ARG;
+    return search_pipelined(refs, n_refs, width, q_bases, q_offsets, q_ref, n_q, out,
+                            reinterpret_cast<cudaStream_t>(stream), params, locate, cap, out_offsets, out_pos,
+                            capacity);
+}
+}  // namespace sa
+
+extern "C" {
+
 int sa_search_batch(const sa_index *const *refs, uint32_t n_refs, const char *q_bases, const uint64_t *q_offsets,
                     const uint32_t *q_ref, uint64_t n_q, sa_result *out, void *stream) {
+    if (sa::pipelined(q_bases, q_offsets, n_q))
+        return sa::search_pipelined_entry(refs, n_refs, q_bases, q_offsets, q_ref, n_q, out, stream, nullptr, false,
+                                          0, nullptr, nullptr, 0);
     return search_impl(refs, n_refs, q_bases, q_offsets, q_ref, n_q, out, stream, nullptr, false);
 }
 
 int sa_search_batch_ex(const sa_index *const *refs, uint32_t n_refs, const char *q_bases, const uint64_t *q_offsets,
                        const uint32_t *q_ref, uint64_t n_q, sa_result *out, void *stream,
                        const sa_search_params *params) {
+    if (sa::pipelined(q_bases, q_offsets, n_q))
+        return sa::search_pipelined_entry(refs, n_refs, q_bases, q_offsets, q_ref, n_q, out, stream, params, false,
+                                          0, nullptr, nullptr, 0);
     return search_impl(refs, n_refs, q_bases, q_offsets, q_ref, n_q, out, stream, params, false);
 }
 
@@ -529,7 +650,34 @@ int sa_search_batch_plain(const sa_index *const *refs, uint32_t n_refs, const ch
     return search_impl(refs, n_refs, q_bases, q_offsets, q_ref, n_q, out, stream, nullptr, true);
 }
 
+}  // extern "C"
+
 namespace sa {
+
+// Locate on device-resident inputs and outputs; base_in (device, or null for
+// 0) is added to every offset, for one chunk of a larger batch.
+int locate_device(const sa_index *const *refs, uint32_t n_refs, uint32_t width, const uint32_t *ref_d,
+                  const sa_result *res_d, uint64_t n_q, uint32_t cap, uint64_t *off_d, void *pos_d,
+                  uint64_t capacity, const uint64_t *base_in, int *overflow, cudaStream_t s, Scratch &sc) {
+    uint64_t *partials = sc.get<uint64_t>(locate_tiles(n_q) + 1);
+    if (sc.failed) return SA_ERR_NOMEM;
+    LocateLaunch L;
+    memset(&L, 0, sizeof L);
+    fill_ref_table(refs, n_refs, 0, &L.refs);
+    L.n_refs = n_refs;
+    L.width = width;
+    L.q_ref = ref_d;
+    L.res = res_d;
+    L.n_q = n_q;
+    L.cap = cap;
+    L.out_offsets = off_d;
+    L.out_pos = pos_d;
+    L.capacity = pos_d ? capacity : 0;
+    L.partials = partials;
+    L.overflow = overflow;
+    L.base_in = base_in;
+    return status_from_cuda(launch_locate(L, s));
+}
 
 int locate_impl(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_ref, const sa_result *res,
                 uint64_t n_q, uint32_t cap, uint64_t *out_offsets, void *out_pos, uint64_t out_pos_capacity,
@@ -550,27 +698,13 @@ int locate_impl(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_
     void *pos_d = out_pos;
     if (!pos_dev && out_pos_capacity) pos_d = sc.get<uint8_t>(out_pos_capacity * width);
     if (!pos_dev && !out_pos_capacity) pos_d = nullptr;
-    const uint64_t tiles = locate_tiles(n_q);
-    uint64_t *partials = sc.get<uint64_t>(tiles + 1);
     int *overflow = dstatus && pos_d ? sc.get<int>(1) : nullptr;
     if (sc.failed) return SA_ERR_NOMEM;
     if (err != cudaSuccess) return status_from_cuda(err);
     if (overflow && (err = cudaMemsetAsync(overflow, 0, sizeof(int), s)) != cudaSuccess) return status_from_cuda(err);
-    LocateLaunch L;
-    memset(&L, 0, sizeof L);
-    fill_ref_table(refs, n_refs, 0, &L.refs);
-    L.n_refs = n_refs;
-    L.width = width;
-    L.q_ref = ref_d;
-    L.res = res_d;
-    L.n_q = n_q;
-    L.cap = cap;
-    L.out_offsets = off_d;
-    L.out_pos = pos_d;
-    L.capacity = pos_d ? out_pos_capacity : 0;
-    L.partials = partials;
-    L.overflow = overflow;
-    if ((err = launch_locate(L, s)) != cudaSuccess) return status_from_cuda(err);
+    st = locate_device(refs, n_refs, width, ref_d, res_d, n_q, cap, off_d, pos_d, out_pos_capacity, nullptr, overflow,
+                       s, sc);
+    if (st) return st;
     if (overflow && (err = launch_capacity_status(overflow, dstatus, s)) != cudaSuccess) return status_from_cuda(err);
     if (!off_dev || !pos_dev) {
         uint64_t total = 0;
@@ -590,7 +724,180 @@ int locate_impl(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_
     return SA_OK;
 }
 
+constexpr int kPipelineStreams = 2;
+
+cudaError_t pipeline_streams(cudaStream_t out[kPipelineStreams]) {
+    static std::mutex mu;
+    static cudaStream_t st[kMaxDevices][kPipelineStreams];
+    static bool ok[kMaxDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ok[dev]) {
+        for (int i = 0; i < kPipelineStreams; i++)
+            if ((e = cudaStreamCreateWithFlags(&st[dev][i], cudaStreamNonBlocking)) != cudaSuccess) return e;
+        ok[dev] = true;
+    }
+    for (int i = 0; i < kPipelineStreams; i++) out[i] = st[dev][i];
+    return cudaSuccess;
+}
+
+// Events of one pipelined call, destroyed when it returns (after the streams
+// that use them have been waited for, or are ordered before the caller's).
+struct Events {
+    std::vector<cudaEvent_t> ev;
+    cudaEvent_t make() {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        ev.push_back(e);
+        return e;
+    }
+    ~Events() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+};
+
+// sa_search_batch / sa_search_locate with q_bases and q_offsets in host
+// memory, in chunks of queries (see kPipelineMinQueries).  Same results,
+// status and synchronization as the unchunked calls.
+int search_pipelined(const sa_index *const *refs, uint32_t n_refs, uint32_t width, const char *q_bases,
+                     const uint64_t *q_offsets, const uint32_t *q_ref, uint64_t n_q, sa_result *out,
+                     cudaStream_t s, const sa_search_params *params, bool locate, uint32_t cap,
+                     uint64_t *out_offsets, void *out_pos, uint64_t capacity) {
+    const uint64_t per = (n_q + 11) / 12 > (1ull << 20) ? (n_q + 11) / 12 : (1ull << 20);
+    const uint64_t n_chunks = (n_q + per - 1) / per;
+    uint64_t max_bases = 0;
+    for (uint64_t c = 0; c < n_chunks; c++) {
+        const uint64_t a = c * per, b = a + per < n_q ? a + per : n_q;
+        if (q_offsets[b] < q_offsets[a]) return SA_ERR_ARG;
+        if (q_offsets[b] - q_offsets[a] > max_bases) max_bases = q_offsets[b] - q_offsets[a];
+    }
+    if (max_bases > 0 && !q_bases) return SA_ERR_ARG;
+    const bool out_dev = on_device(out);
+    if (out_dev && ((uintptr_t)out & 31u)) return SA_ERR_ARG;
+    const bool ref_dev = q_ref && on_device(q_ref);
+    const bool off_dev = !locate || on_device(out_offsets);
+    const bool pos_dev = !locate || out_pos == nullptr || on_device(out_pos);
+    int *dstatus = params ? params->device_status : nullptr;
+    if (dstatus && !on_device(dstatus)) return SA_ERR_ARG;
+    sa_search_params cp;  // the caller's knobs, without the per-call extras the chunks do not take
+    memset(&cp, 0, sizeof cp);
+    if (params) cp = *params;
+    cp.search_events[0] = cp.search_events[1] = nullptr;
+    cp.device_status = nullptr;
+    cp.flags &= ~SA_PARAM_Q_RANGE;
+    // the order is decided for the whole batch, not per chunk
+    const uint32_t order = cp.flags & (SA_PARAM_KMER_ORDER | SA_PARAM_INPUT_ORDER);
+    if (order == (SA_PARAM_KMER_ORDER | SA_PARAM_INPUT_ORDER)) return SA_ERR_ARG;
+    if (use_kmer_order(refs, n_refs, n_q, order)) cp.flags = (cp.flags & ~SA_PARAM_INPUT_ORDER) | SA_PARAM_KMER_ORDER;
+
+    cudaStream_t ts[kPipelineStreams];
+    cudaError_t err = pipeline_streams(ts);
+    if (err != cudaSuccess) return status_from_cuda(err);
+    Events evs;
+    int st = SA_OK;
+    uint64_t total = 0;
+    int hstat[2] = {0, 0};
+    {
+        Scratch sc{s};
+        sa_result *out_d = out_dev ? out : sc.get<sa_result>(n_q);
+        uint64_t *off_d = off_dev ? out_offsets : sc.get<uint64_t>(n_q + 1);
+        void *pos_d = pos_dev ? out_pos : (capacity ? sc.get<uint8_t>(capacity * width) : nullptr);
+        char *slot_bases[kPipelineStreams];
+        uint64_t *slot_off[kPipelineStreams];
+        uint32_t *slot_ref[kPipelineStreams];
+        for (int i = 0; i < kPipelineStreams; i++) {
+            slot_bases[i] = sc.get<char>(max_bases);
+            slot_off[i] = sc.get<uint64_t>(per + 1);
+            slot_ref[i] = q_ref && !ref_dev ? sc.get<uint32_t>(per) : nullptr;
+        }
+        // [0] the chunks' statuses folded (the highest precedence seen), [1]
+        // capacity overflow, then a zero base for the first chunk's offsets
+        int *stat_d = sc.get<int>(4);
+        if (sc.failed) return SA_ERR_NOMEM;
+        const uint64_t *zero = reinterpret_cast<const uint64_t *>(stat_d + 2);
+        if ((err = cudaMemsetAsync(stat_d, 0, 4 * sizeof(int), s)) != cudaSuccess) return status_from_cuda(err);
+        cudaEvent_t start = evs.make(), loc_done[kPipelineStreams], fin[kPipelineStreams];
+        for (int i = 0; i < kPipelineStreams; i++) {
+            loc_done[i] = evs.make();
+            fin[i] = evs.make();
+        }
+        if (!start || evs.ev.size() != 1 + 2 * kPipelineStreams) return SA_ERR_CUDA;
+        if ((err = cudaEventRecord(start, s)) != cudaSuccess) return status_from_cuda(err);
+        for (int i = 0; i < kPipelineStreams; i++)
+            if ((err = cudaStreamWaitEvent(ts[i], start, 0)) != cudaSuccess) return status_from_cuda(err);
+        for (uint64_t c = 0; c < n_chunks && st == SA_OK; c++) {
+            const int i = (int)(c % kPipelineStreams);
+            cudaStream_t t = ts[i];
+            const uint64_t a = c * per, b = a + per < n_q ? a + per : n_q, nq = b - a;
+            const uint64_t ba = q_offsets[a], nb = q_offsets[b] - ba;
+            if (nb && (err = cudaMemcpyAsync(slot_bases[i], q_bases + ba, nb, cudaMemcpyHostToDevice, t)) != cudaSuccess)
+                break;
+            if ((err = cudaMemcpyAsync(slot_off[i], q_offsets + a, (nq + 1) * 8, cudaMemcpyHostToDevice, t)) !=
+                cudaSuccess)
+                break;
+            const uint32_t *ref_c = q_ref ? (ref_dev ? q_ref + a : slot_ref[i]) : nullptr;
+            if (q_ref && !ref_dev &&
+                (err = cudaMemcpyAsync(slot_ref[i], q_ref + a, nq * 4, cudaMemcpyHostToDevice, t)) != cudaSuccess)
+                break;
+            Scratch csc{t};
+            int *flags = nullptr;
+            st = search_device(refs, n_refs, width, slot_bases[i], slot_off[i], ref_c, nq, ba, nb, out_d + a, t, &cp,
+                               false, locate ? cap : ~0u, csc, &flags);
+            if (st) break;
+            if ((err = launch_fold_status(flags, stat_d, t)) != cudaSuccess) break;
+            if (locate) {
+                if (c > 0 && (err = cudaStreamWaitEvent(t, loc_done[(c - 1) % kPipelineStreams], 0)) != cudaSuccess)
+                    break;
+                st = locate_device(refs, n_refs, width, ref_c, out_d + a, nq, cap, off_d + a, pos_d, capacity,
+                                   c ? off_d + a : zero, stat_d + 1, t, csc);
+                if (st) break;
+                if ((err = cudaEventRecord(loc_done[i], t)) != cudaSuccess) break;
+                if (!off_dev && (err = cudaMemcpyAsync(out_offsets + a, off_d + a, nq * 8, cudaMemcpyDeviceToHost,
+                                                       t)) != cudaSuccess)
+                    break;
+            }
+            if (!out_dev && (err = cudaMemcpyAsync(out + a, out_d + a, nq * sizeof(sa_result), cudaMemcpyDeviceToHost,
+                                                   t)) != cudaSuccess)
+                break;
+        }
+        // join the library streams into the caller's
+        for (int i = 0; i < kPipelineStreams; i++) {
+            cudaError_t e = cudaEventRecord(fin[i], ts[i]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fin[i], 0);
+            if (e != cudaSuccess && err == cudaSuccess) err = e;
+        }
+        if (st) return st;
+        if (err != cudaSuccess) return status_from_cuda(err);
+        if (dstatus && (err = launch_fold_final(stat_d, locate && pos_d, dstatus, s)) != cudaSuccess)
+            return status_from_cuda(err);
+        const bool host_out = !out_dev || !off_dev || !pos_dev;
+        if (host_out) {
+            if (locate && (err = cudaMemcpyAsync(&total, off_d + n_q, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+                return status_from_cuda(err);
+            if ((err = cudaMemcpyAsync(hstat, stat_d, sizeof hstat, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+                return status_from_cuda(err);
+            if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return status_from_cuda(err);
+            if (locate && !off_dev) out_offsets[n_q] = total;
+            const uint64_t kept = total < capacity ? total : capacity;
+            if (locate && !pos_dev && pos_d && kept) {
+                if ((err = cudaMemcpyAsync(out_pos, pos_d, kept * width, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+                    return status_from_cuda(err);
+                if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return status_from_cuda(err);
+            }
+        }
+        if (!host_out) return SA_OK;
+    }
+    if (hstat[0]) return hstat[0] == 3 ? SA_ERR_TIMEOUT : hstat[0] == 2 ? SA_ERR_BASE : SA_ERR_ARG;
+    if (locate && out_pos && total > capacity) return SA_ERR_CAPACITY;
+    return SA_OK;
+}
+
 }  // namespace sa
+
+extern "C" {
 
 int sa_locate(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_ref, const sa_result *res,
               uint64_t n_q, uint32_t cap, uint64_t *out_offsets, void *out_pos, uint64_t out_pos_capacity,
@@ -602,9 +909,12 @@ int sa_search_locate(const sa_index *const *refs, uint32_t n_refs, const char *q
                      const uint32_t *q_ref, uint64_t n_q, sa_result *out, uint32_t cap, uint64_t *out_offsets,
                      void *out_pos, uint64_t out_pos_capacity, void *stream, const sa_search_params *params) {
     using namespace sa;
-    NvtxRange range("sa_search_locate");
     if (!out_offsets || (n_q && !out)) return SA_ERR_ARG;
-    const int st = search_impl(refs, n_refs, q_bases, q_offsets, q_ref, n_q, out, stream, params, false);
+    if (pipelined(q_bases, q_offsets, n_q))
+        return search_pipelined_entry(refs, n_refs, q_bases, q_offsets, q_ref, n_q, out, stream, params, true, cap,
+                                      out_offsets, out_pos, out_pos_capacity);
+    NvtxRange range("sa_search_locate");
+    const int st = search_impl(refs, n_refs, q_bases, q_offsets, q_ref, n_q, out, stream, params, false, cap);
     if (st && st != SA_ERR_BASE && st != SA_ERR_ARG) return st;
     // invalid queries carry the all-ones result (no positions); the rest are located
     int *dstatus = params ? params->device_status : nullptr;
@@ -782,6 +1092,43 @@ void sa_free(sa_index *idx) {
     if (!idx) return;
     cudaDeviceSynchronize();
     free_index(idx);
+}
+
+int sa_search_order(const sa_index *const *refs, uint32_t n_refs, uint64_t n_q, const sa_search_params *params,
+                    int *kmer_order) {
+    uint32_t width = 0;
+    int st = check_refs(refs, n_refs, &width);
+    if (st) return st;
+    if (!kmer_order) return SA_ERR_ARG;
+    const uint32_t order = params ? params->flags & (SA_PARAM_KMER_ORDER | SA_PARAM_INPUT_ORDER) : 0u;
+    if (order == (SA_PARAM_KMER_ORDER | SA_PARAM_INPUT_ORDER)) return SA_ERR_ARG;
+    *kmer_order = use_kmer_order(refs, n_refs, n_q, order) ? 1 : 0;
+    return SA_OK;
+}
+
+int sa_scratch_info(uint64_t *reserved_bytes, uint64_t *used_bytes, uint64_t *used_high_bytes, int reset_high) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SA_ERR_CUDA;
+    cudaMemPool_t pool = scratch_pool(dev);
+    if (!pool) return SA_ERR_CUDA;
+    uint64_t v = 0;  // the attributes are 64-bit (cuuint64_t)
+    if (reserved_bytes) {
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &v) != cudaSuccess) return SA_ERR_CUDA;
+        *reserved_bytes = v;
+    }
+    if (used_bytes) {
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v) != cudaSuccess) return SA_ERR_CUDA;
+        *used_bytes = v;
+    }
+    if (used_high_bytes) {
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &v) != cudaSuccess) return SA_ERR_CUDA;
+        *used_high_bytes = v;
+    }
+    if (reset_high) {
+        uint64_t zero = 0;
+        if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero) != cudaSuccess) return SA_ERR_CUDA;
+    }
+    return SA_OK;
 }
 
 const char *sa_strerror(int status) {

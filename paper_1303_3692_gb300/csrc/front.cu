@@ -35,20 +35,6 @@ struct FrontDesc {
     uint32_t kmer_k;
 };
 
-__device__ __forceinline__ void write_result(sa_result *out, uint64_t q, uint64_t lo, uint64_t hi) {
-    sa_result r;
-    r.lo = lo;
-    r.hi = hi;
-    r.count = (lo == ~0ull) ? ~0ull : hi - lo;
-    out[q] = r;
-}
-
-// Bits [lo, hi) of a 32-bit mask (0 <= lo <= hi <= 32).
-__device__ __forceinline__ uint32_t bit_range(uint32_t lo, uint32_t hi) {
-    const uint32_t upto = hi >= 32u ? 0xFFFFFFFFu : ((1u << hi) - 1u);
-    return upto & ~((1u << lo) - 1u);
-}
-
 // P (bases 0-127 in w, the rest at base qa of the packed batch; length m >=
 // 1) against the pivot of a k-mer entry: its first 192 bases in e (clamp of
 // them exist), then the text from position pos + 192 when all 192 tie.
@@ -67,7 +53,10 @@ __device__ __forceinline__ int cmp_entry(const uint64_t w[4], uint32_t m, const 
     return cmp_suffix_tq(T, n, pos, tq, qa, m, 192u, lcp);
 }
 
-template <bool kSingle>
+// kFromList: the queries come from the k-mer-ordered list of bucket.cu (one
+// 64-byte record each: length, index, reference, first base in the packed
+// batch and first 128 bases, already checked) instead of the batch's offsets.
+template <bool kSingle, bool kFromList>
 __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_constant__ SearchLaunch a) {
     __shared__ FrontDesc sdesc[SA_MAX_REFS];
     __shared__ uint4 s_stage[kFrontThreads / 32][32][4];  // worklist records staged per warp
@@ -99,66 +88,60 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
     const uint64_t *__restrict__ tq = a.tq;
     bool any_bad = false, any_bad_ref = false;
 
+    const uint64_t n_items = kFromList ? (uint64_t)*a.wl_in_count : a.n_q;
     // Offsets and reference of this lane's next query, read one query ahead.
     uint64_t nqa = 0, nqe = 0;
     uint32_t nr = 0;
-    if (warp_first + lane < a.n_q) {
+    if (!kFromList && warp_first + lane < a.n_q) {
         nqa = __ldg(a.q_off + warp_first + lane);
         nqe = __ldg(a.q_off + warp_first + lane + 1);
         if (!kSingle) nr = __ldg(a.q_ref + warp_first + lane);
     }
 
-    for (uint64_t base = warp_first; base < a.n_q; base += stride) {
-        const uint64_t q = base + lane;
-        const bool live = q < a.n_q;
-        uint64_t qa = nqa - a.first, qe = nqe - a.first;
-        const uint32_t r = nr;
-        if (base + stride + lane < a.n_q) {
-            nqa = __ldg(a.q_off + base + stride + lane);
-            nqe = __ldg(a.q_off + base + stride + lane + 1);
-            if (!kSingle) nr = __ldg(a.q_ref + base + stride + lane);
-        }
-        const bool range_ok = live && qa <= qe && qe <= a.total && qe - qa < (1ull << 31);
-        if (live && !range_ok) any_bad = true;
-        if (range_ok && a.revcomp) {  // the reverse complement sits at the mirrored range
-            const uint64_t t = a.total - qe;
-            qe = a.total - qa;
-            qa = t;
-        }
-        bool ok = range_ok && r < a.n_refs;
-        if (range_ok && r >= a.n_refs) any_bad_ref = true;
-        const uint32_t m = ok ? (uint32_t)(qe - qa) : 0u;
-
-        // First 128 bases and the validity of every base of the query.
-        const uint64_t w_lo = ok ? (qa >> 5) : 0;
-        const uint32_t sh = (uint32_t)(qa & 31u) * 2u;
-        uint64_t t[5];
-        uint32_t v[5];
-#pragma unroll
-        for (int i = 0; i < 5; i++) {
-            t[i] = __ldg(tq + w_lo + i);
-            v[i] = __ldg(a.tv + w_lo + i);
-        }
+    for (uint64_t base = warp_first; base < n_items; base += stride) {
+        const bool live = base + lane < n_items;
+        uint64_t q, qa;
+        uint32_t r, m;
+        bool ok, entry = true;
         uint64_t w[4];
-#pragma unroll
-        for (int j = 0; j < 4; j++) w[j] = (t[j] << sh) | ((t[j + 1] >> 1) >> (63u - sh));
-        if (ok && m > 0) {
-            const uint32_t b0 = (uint32_t)(qa & 31u);  // the query's first bit in word w_lo
-            uint32_t badbits = 0;
-#pragma unroll
-            for (int i = 0; i < 5; i++) {
-                const uint32_t lo = i == 0 ? b0 : 0u;
-                const uint64_t end = (uint64_t)b0 + m;  // one past the query's last bit, from word w_lo
-                const uint64_t wend = 32ull * (i + 1);
-                const uint32_t hi = end >= wend ? 32u : (end > 32ull * i ? (uint32_t)(end - 32ull * i) : 0u);
-                if (hi > lo) badbits |= v[i] & bit_range(lo, hi);
+        if (kFromList) {
+            uint4 c0, c1, c2, c3;
+            const uint4 *src = a.wrec_in + 4 * (size_t)(base + lane);
+            ldg32_if(live, src, &c0, &c1);
+            ldg32_if(live, src + 2, &c2, &c3);
+            q = c0.w;
+            m = c0.z;
+            r = c1.x;
+            entry = (c1.y & kRecNeedsEntry) != 0u;
+            qa = ((uint64_t)c1.w << 32) | c1.z;
+            w[0] = ((uint64_t)c2.y << 32) | c2.x;
+            w[1] = ((uint64_t)c2.w << 32) | c2.z;
+            w[2] = ((uint64_t)c3.y << 32) | c3.x;
+            w[3] = ((uint64_t)c3.w << 32) | c3.z;
+            ok = live;
+        } else {
+            q = base + lane;
+            qa = nqa - a.first;
+            uint64_t qe = nqe - a.first;
+            r = nr;
+            if (base + stride + lane < a.n_q) {
+                nqa = __ldg(a.q_off + base + stride + lane);
+                nqe = __ldg(a.q_off + base + stride + lane + 1);
+                if (!kSingle) nr = __ldg(a.q_ref + base + stride + lane);
             }
-            for (uint64_t i = 5; 32ull * i < (uint64_t)b0 + m; i++) {  // queries longer than 128 bases
-                const uint64_t end = (uint64_t)b0 + m;
-                const uint32_t hi = end >= 32ull * (i + 1) ? 32u : (uint32_t)(end - 32ull * i);
-                badbits |= __ldg(a.tv + w_lo + i) & bit_range(0, hi);
+            const bool range_ok = live && qa <= qe && qe <= a.total && qe - qa < (1ull << 31);
+            if (live && !range_ok) any_bad = true;
+            if (range_ok && a.revcomp) {  // the reverse complement sits at the mirrored range
+                const uint64_t t = a.total - qe;
+                qe = a.total - qa;
+                qa = t;
             }
-            if (badbits) {
+            ok = range_ok && r < a.n_refs;
+            if (range_ok && r >= a.n_refs) any_bad_ref = true;
+            m = ok ? (uint32_t)(qe - qa) : 0u;
+
+            // First 128 bases and the validity of every base of the query.
+            if (!load_query_head(tq, a.tv, ok ? (qa >> 5) : 0, (uint32_t)(qa & 31u), m, ok && m > 0, w)) {
                 ok = false;
                 any_bad = true;
             }
@@ -168,7 +151,7 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
         if (!kSingle && ok) d = sdesc[r];
         // Bracket and first pivot: the k-mer entry for m >= k, else the whole array.
         const uint32_t kk = d.kmer_k;
-        const bool look = ok && m > 0 && d.krt != nullptr && m >= kk;
+        const bool look = ok && entry && m > 0 && d.krt != nullptr && m >= kk;
         const uint64_t x = look ? (w[0] >> (64u - 2u * kk)) : 0ull;
         uint4 h, e01, e23, e45;
         ldg32_if(look, d.krt + 4 * x, &h, &e01);
@@ -177,9 +160,9 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
         uint32_t R = look ? h.y : d.n;
 
         bool done = !live || !ok || m == 0 || (look && R - L <= 1u);
-        if (live && !ok) write_result(a.out, q, ~0ull, ~0ull);
-        if (live && ok && m == 0) write_result(a.out, q, 0, d.n);
-        if (live && ok && m > 0 && look && R - L <= 1u) write_result(a.out, q, R, R);
+        if (live && !ok) store_result(a.out, q, ~0ull, ~0ull, a.trunc_cap);
+        if (live && ok && m == 0) store_result(a.out, q, 0, d.n, a.trunc_cap);
+        if (live && ok && m > 0 && look && R - L <= 1u) store_result(a.out, q, R, R, a.trunc_cap);
 
         uint32_t lcpL = 0, lcpR = 0, HL = 0, HR = 0, hlcpL = 0, hlcpR = 0, lo = 0, phase = 0;
         bool go = !done && look;
@@ -210,7 +193,7 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
                     phase = 2;
                 }
                 if (R - L <= 1u) {
-                    write_result(a.out, q, phase == 0 ? R : lo, R);
+                    store_result(a.out, q, phase == 0 ? R : lo, R, a.trunc_cap);
                     done = true;
                     go = false;
                 }
@@ -267,8 +250,10 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
         }
     }
     flush(staged);
-    if (__any_sync(0xFFFFFFFFu, any_bad) && lane == 0) atomicOr(a.pack_err, 1);
-    if (__any_sync(0xFFFFFFFFu, any_bad_ref) && lane == 0) atomicOr(a.bad_ref, 1);
+    if (!kFromList) {
+        if (__any_sync(0xFFFFFFFFu, any_bad) && lane == 0) atomicOr(a.pack_err, 1);
+        if (__any_sync(0xFFFFFFFFu, any_bad_ref) && lane == 0) atomicOr(a.bad_ref, 1);
+    }
 }
 
 }  // namespace
@@ -276,17 +261,17 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
 cudaError_t launch_front(const SearchLaunch &L, cudaStream_t s) {
     if (L.n_q == 0) return cudaSuccess;
     const bool single = L.n_refs == 1 && L.q_ref == nullptr;
-    static int per_sm[2][64] = {};
+    const bool list = L.wrec_in != nullptr;
+    static int per_sm[4][64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    int &bps = per_sm[single ? 1 : 0][dev];
+    auto kernel = single ? (list ? front_kernel<true, true> : front_kernel<true, false>)
+                         : (list ? front_kernel<false, true> : front_kernel<false, false>);
+    int &bps = per_sm[(single ? 1 : 0) + (list ? 2 : 0)][dev];
     if (bps == 0) {
         int b = 0;
-        const cudaError_t e = single ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, front_kernel<true>,
-                                                                                    kFrontThreads, 0)
-                                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, front_kernel<false>,
-                                                                                    kFrontThreads, 0);
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kFrontThreads, 0);
         if (e != cudaSuccess) return e;
         bps = b > 0 ? b : 1;
     }
@@ -294,10 +279,7 @@ cudaError_t launch_front(const SearchLaunch &L, cudaStream_t s) {
     const uint64_t cap = (uint64_t)device_sm_count() * bps;
     uint64_t blocks = (warps + kFrontThreads / 32 - 1) / (kFrontThreads / 32);
     if (blocks > cap) blocks = cap;
-    if (single)
-        front_kernel<true><<<(unsigned)blocks, kFrontThreads, 0, s>>>(L);
-    else
-        front_kernel<false><<<(unsigned)blocks, kFrontThreads, 0, s>>>(L);
+    kernel<<<(unsigned)blocks, kFrontThreads, 0, s>>>(L);
     return cudaGetLastError();
 }
 

@@ -73,10 +73,12 @@ __global__ void __launch_bounds__(kTileThreads) tile_sums_kernel(const sa_result
     if (threadIdx.x == 0) partials[blockIdx.x] = total;
 }
 
-// One CTA: exclusive scan of the tile sums in place; partials[ntiles] = total.
-__global__ void __launch_bounds__(1024) scan_partials_kernel(uint64_t *partials, uint64_t ntiles) {
+// One CTA: exclusive scan of the tile sums in place, starting from *base_in
+// (0 when null); partials[ntiles] = base + total.
+__global__ void __launch_bounds__(1024) scan_partials_kernel(uint64_t *partials, uint64_t ntiles,
+                                                             const uint64_t *base_in) {
     __shared__ uint64_t carry_s;
-    if (threadIdx.x == 0) carry_s = 0;
+    if (threadIdx.x == 0) carry_s = base_in ? *base_in : 0;
     __syncthreads();
     for (uint64_t base = 0; base < ntiles; base += blockDim.x) {
         const uint64_t i = base + threadIdx.x;
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_gather_kernel(const __gr
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
         const uint64_t q = warp_base + (uint64_t)i * 32 + lane;
-        sa_result r{0, 0, 0};
+        sa_result r{0, 0, 0, 0};
         if (q < a.n_q) r = a.res[q];
         const uint32_t k = q < a.n_q ? (uint32_t)kept(r, a.cap) : 0u;  // cap is 32-bit
         uint64_t x = k;
@@ -167,6 +169,17 @@ cudaError_t locate_static_partials(uint64_t **ptr, uint64_t *entries) {
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(mu);
+    if (addr[dev]) {
+        // A device reset unloads the module; the array may then live at another
+        // address.  The cached one is kept only while it is still device memory
+        // of this device.
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, addr[dev]) != cudaSuccess || at.type != cudaMemoryTypeDevice ||
+            at.device != dev) {
+            cudaGetLastError();
+            addr[dev] = nullptr;
+        }
+    }
     if (!addr[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_partials);
@@ -185,7 +198,7 @@ cudaError_t launch_locate(const LocateLaunch &L, cudaStream_t s) {
         return cudaMemsetAsync(L.out_offsets, 0, sizeof(uint64_t), s);
     }
     tile_sums_kernel<<<(unsigned)tiles, kTileThreads, 0, s>>>(L.res, L.n_q, L.cap, L.partials);
-    scan_partials_kernel<<<1, 1024, 0, s>>>(L.partials, tiles);
+    scan_partials_kernel<<<1, 1024, 0, s>>>(L.partials, tiles, L.base_in);
     if (L.width == 4)
         tile_gather_kernel<uint32_t><<<(unsigned)tiles, kTileThreads, 0, s>>>(L);
     else

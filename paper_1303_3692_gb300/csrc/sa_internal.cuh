@@ -40,7 +40,14 @@ struct RefDesc {
     uint32_t smem_off;      // byte offset of this table in the search kernel's shared memory
     uint32_t use_depth;     // depth the search uses (<= depth); 0 = no table
     uint32_t kmer_k;        // k of the k-mer table (0: none)
+    uint64_t kbase;         // k-mer entries of the earlier indexes of the call (k-mer order buckets)
 };
+
+// k-mer order of a batch (bucket.cu): the slices of the k-mer entries of a
+// call's indexes, plus one bucket for queries without a k-mer bracket.
+constexpr uint32_t kNumBuckets = 256;
+// Worklist record flag ({ref, flags, qa}): read the query's k-mer entry first.
+constexpr uint32_t kRecNeedsEntry = 1u;
 
 // The compare outcome of the three cases of Section IV.
 enum : int { CMP_LESS = -1, CMP_PREFIX = 0, CMP_GREATER = 1 };
@@ -134,6 +141,63 @@ __device__ __forceinline__ uint64_t pack_word(const uint8_t *__restrict__ a, uin
         }
     }
     return word;
+}
+
+// Bits [lo, hi) of a 32-bit mask (0 <= lo <= hi <= 32).
+__device__ __forceinline__ uint32_t bit_range(uint32_t lo, uint32_t hi) {
+    const uint32_t upto = hi >= 32u ? 0xFFFFFFFFu : ((1u << hi) - 1u);
+    return upto & ~((1u << lo) - 1u);
+}
+
+// The head of a query of the packed batch: its first 128 bases as four
+// packed words w[0..3] (base 0 in the top bits of w[0]; bits past the query
+// hold the batch's next bases), read as five words from word w_lo = qa / 32
+// of tq with the shift of qa % 32.  With check set, returns whether all m
+// bases (from bit qa % 32 of word w_lo on) are marked valid in the per-word
+// masks tv; else returns true without reading past the five words.
+__device__ __forceinline__ bool load_query_head(const uint64_t *__restrict__ tq, const uint32_t *__restrict__ tv,
+                                                uint64_t w_lo, uint32_t b0, uint32_t m, bool check,
+                                                uint64_t w[4]) {
+    const uint32_t sh = b0 * 2u;
+    uint64_t t[5];
+    uint32_t v[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        t[i] = __ldg(tq + w_lo + i);
+        v[i] = __ldg(tv + w_lo + i);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; j++) w[j] = (t[j] << sh) | ((t[j + 1] >> 1) >> (63u - sh));
+    if (!check) return true;
+    uint32_t badbits = 0;
+    const uint64_t end = (uint64_t)b0 + m;  // one past the query's last bit, from word w_lo
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        const uint32_t lo = i == 0 ? b0 : 0u;
+        const uint64_t wend = 32ull * (i + 1);
+        const uint32_t hi = end >= wend ? 32u : (end > 32ull * i ? (uint32_t)(end - 32ull * i) : 0u);
+        if (hi > lo) badbits |= v[i] & bit_range(lo, hi);
+    }
+    for (uint64_t i = 5; 32ull * i < end; i++) {  // queries longer than 128 bases
+        const uint32_t hi = end >= 32ull * (i + 1) ? 32u : (uint32_t)(end - 32ull * i);
+        badbits |= __ldg(tv + w_lo + i) & bit_range(0, hi);
+    }
+    return badbits == 0;
+}
+
+// One query's result, written as one 32-byte store (a whole DRAM sector, so a
+// result at a random slot needs no read-modify-write): [lo, hi), count and
+// flags; lo = ~0 marks an invalid query (all-ones result).  trunc_cap: the
+// call's locate cap (a count above it sets SA_RESULT_TRUNCATED), or ~0u.
+__device__ __forceinline__ void store_result(sa_result *out, uint64_t q, uint64_t lo, uint64_t hi,
+                                             uint32_t trunc_cap) {
+    const bool bad = lo == ~0ull;
+    const uint64_t count = bad ? ~0ull : hi - lo;
+    const uint64_t flags = bad ? (uint64_t)SA_RESULT_INVALID
+                               : (count > (uint64_t)trunc_cap ? (uint64_t)SA_RESULT_TRUNCATED : 0ull);
+    asm volatile("st.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(out + q), "l"(lo), "l"(hi), "l"(count),
+                 "l"(flags)
+                 : "memory");
 }
 
 // One 32-byte (one DRAM sector) read-only load; p must be 32-byte aligned.
@@ -308,6 +372,8 @@ struct SearchLaunch {
     uint64_t n_q;
     uint4 *wrec;              // worklist records, 64 bytes (4 uint4) each, n_q of room
     uint32_t *wl_count;       // device: records in the worklist
+    const uint4 *wrec_in;     // k-mer order: the batch's queries as records (first pass input), or null
+    uint32_t *wl_in_count;    // k-mer order: records in wrec_in
     sa_result *out;
     int *pack_err;            // device flag: some query had a non-ACGT byte or bad offsets
     int *bad_ref;             // device flag: some query named a reference id >= n_refs
@@ -318,6 +384,12 @@ struct SearchLaunch {
     uint32_t front_probes;    // probes per query in the first pass
     bool revcomp;             // search every query's reverse complement (the batch is packed reversed)
     bool expire_waits;        // test hook: the bounded key-table wait gives up at once
+    uint32_t trunc_cap;       // the locate cap of sa_search_locate (SA_RESULT_TRUNCATED), else ~0u
+    // k-mer order (bucket.cu)
+    uint64_t ktotal;          // k-mer entries of all indexes of the call
+    uint16_t *qbucket;        // per query: its bucket
+    uint32_t *bhist;          // kNumBuckets + 1 bucket totals (zeroed by the caller)
+    uint32_t *bcursor;        // kNumBuckets + 1 next free worklist slots
 };
 // Worklist record of a query the first pass did not finish (64 bytes):
 //   {L, R, m, q}            a bracket (L, R) holding both bounds (L = -1 is
@@ -326,12 +398,21 @@ struct SearchLaunch {
 //   {w0, w1}, {w2, w3}      its first 128 bases (packed words)
 cudaError_t launch_pack_batch(const SearchLaunch &L, uint64_t *tq, uint32_t *tv, cudaStream_t s);
 cudaError_t launch_front(const SearchLaunch &L, cudaStream_t s);
+// The batch's queries as records in k-mer order (wrec_in), the first pass's
+// input in that order.
+cudaError_t launch_bucketed_worklist(const SearchLaunch &L, uint4 *wrec_in, cudaStream_t s);
 cudaError_t launch_search(const SearchLaunch &L, cudaStream_t s);
 cudaError_t launch_search_plain(const SearchLaunch &L, cudaStream_t s);
 // One thread: *dst = the call's status from its device flags (flags[1] a
 // wait that ran out, flags[0] a query that is not bases, flags[3] a bad
 // reference id), in that order of precedence.
 cudaError_t launch_search_status(const int *flags, int *dst, cudaStream_t s);
+// One thread each: fold one chunk's device flags into acc[0] (an atomic max
+// of the status's precedence: 3 TIMEOUT, 2 BASE, 1 ARG, 0 OK), so that chunks
+// on several streams fold into one word; then *dst = the status of acc[0], or
+// SA_ERR_CAPACITY when that is SA_OK and check_overflow and acc[1] is set.
+cudaError_t launch_fold_status(const int *flags, int *acc, cudaStream_t s);
+cudaError_t launch_fold_final(const int *acc, bool check_overflow, int *dst, cudaStream_t s);
 // One thread: *dst = SA_ERR_CAPACITY when *overflow is set and *dst is SA_OK.
 cudaError_t launch_capacity_status(const int *overflow, int *dst, cudaStream_t s);
 uint32_t search_table_bytes(uint32_t depth);  // shared-memory bytes of a depth-d key table
@@ -348,6 +429,7 @@ struct LocateLaunch {
     uint64_t capacity;
     uint64_t *partials;       // scratch: one entry per scan tile + 1
     int *overflow;            // optional device flag: a position fell at or beyond capacity
+    const uint64_t *base_in;  // optional device value added to every offset (a chunk of a larger batch)
 };
 uint64_t locate_tiles(uint64_t n_q);
 // Device address of the static scratch of sa_locate_noalloc on the current

@@ -21,9 +21,10 @@
 //     therefore keep 32 independent random probes in flight per load
 //     instruction.
 //
-// search_plain_kernel (comparison point).  Alg. 1 as printed, on a GPU: one
-//   thread per query, two full binary searches over [-1, n), bases compared
-//   one at a time.
+// search_plain_kernel (comparison point).  The paper's direct scheme
+//   (Section IV): one thread per query, two independent binary searches over
+//   the whole suffix array (lower and upper bound of the query), bases
+//   compared one at a time against the text.
 #include <type_traits>
 
 #include "sa_internal.cuh"
@@ -138,14 +139,6 @@ __device__ __forceinline__ int cmp_key(uint64_t q0, uint64_t q1, uint32_t m, uin
     return CMP_PREFIX;
 }
 
-__device__ __forceinline__ void write_result(sa_result *out, uint64_t q, uint64_t lo, uint64_t hi) {
-    sa_result r;
-    r.lo = lo;
-    r.hi = hi;
-    r.count = (lo == ~0ull) ? ~0ull : hi - lo;
-    out[q] = r;
-}
-
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s for the key-table copy
 
 // The search of one query is a sequence of steps, one per loop iteration of
@@ -169,26 +162,10 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s for the key-table copy
 // (HL, HR) until phase 1 ends (phase 2).
 // Warps take chunks of worklist entries from one global counter, each
 // chunk's base fetched while the previous chunk is handed out.
-// Launch-bound variants: kOcc = 1 (1024 threads, <= 64 registers), 3 (512
-// threads x 3 CTAs, <= 40 registers), 8 (256 threads x 8 CTAs, <= 32 registers).
-template <int kOcc>
-struct Occ;
-template <>
-struct Occ<1> {
-    static constexpr int threads = 1024, blocks = 1;
-};
-template <>
-struct Occ<3> {
-    static constexpr int threads = 512, blocks = 3;
-};
-template <>
-struct Occ<8> {
-    static constexpr int threads = 256, blocks = 8;
-};
-
-template <typename IdxT, bool kSingle, int kOcc>
-__global__ void __launch_bounds__(Occ<kOcc>::threads, Occ<kOcc>::blocks)
-    search_kernel(const __grid_constant__ SearchLaunch a) {
+// Launch bounds: 1024 threads, one CTA per SM, at most 64 registers (no
+// spills); smaller CTAs may share an SM up to 1024 threads in all.
+template <typename IdxT, bool kSingle>
+__global__ void __launch_bounds__(1024, 1) search_kernel(const __grid_constant__ SearchLaunch a) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ SmemDesc sdesc[SA_MAX_REFS];
     __shared__ __align__(8) uint64_t mbar;
@@ -364,15 +341,15 @@ __global__ void __launch_bounds__(Occ<kOcc>::threads, Occ<kOcc>::blocks)
             }
             if (R - L <= 1u) {
                 const uint32_t lo_out = phase == 0 ? R : lo;
-                write_result(a.out, qout, lo_out, R);
+                store_result(a.out, qout, lo_out, R, a.trunc_cap);
                 active = false;
             }
         }
     }
 }
 
-// Alg. 1: compare the query (bases qa.. of the packed batch) with the
-// m-prefix of S_p one base at a time.
+// The query (bases qa.. of the packed batch) against the m-prefix of S_p,
+// one base at a time (the three cases of Section IV).
 __device__ __forceinline__ int cmp_plain(const uint64_t *__restrict__ T, uint64_t n, uint64_t p,
                                          const uint64_t *__restrict__ tq, uint64_t qa, uint32_t m) {
     for (uint32_t k = 0; k < m; k++) {
@@ -407,35 +384,33 @@ __global__ void __launch_bounds__(256) search_plain_kernel(const __grid_constant
     if (bad || r >= a.n_refs) {
         if (bad) atomicOr(a.pack_err, 1);
         if (!bad) atomicOr(a.bad_ref, 1);
-        write_result(a.out, q, ~0ull, ~0ull);
+        store_result(a.out, q, ~0ull, ~0ull, a.trunc_cap);
         return;
     }
     const uint32_t m = (uint32_t)(a1 - a0);
     const RefDesc &d = a.refs.r[r];
     const uint64_t *T = d.text;
     const uint64_t n = d.n;
-    // LB: R moves to the pivot while P <= m-prefix of its suffix.
-    int64_t L = -1, R = (int64_t)n;
-    while (R > L + 1) {
-        const int64_t pivot = (L + R) >> 1;
-        if (cmp_plain(T, n, sa_at<IdxT>(d.sa, (uint64_t)pivot), a.tq, a0, m) <= 0)
-            R = pivot;
+    // Lower bound: the first rank whose suffix's m-prefix is not below P.
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (cmp_plain(T, n, sa_at<IdxT>(d.sa, mid), a.tq, a0, m) == CMP_GREATER)
+            lo = mid + 1;
         else
-            L = pivot;
+            hi = mid;
     }
-    const int64_t LB = R;
-    // RB: R moves to the pivot while P < m-prefix of its suffix.
-    L = -1;
-    R = (int64_t)n;
-    while (R > L + 1) {
-        const int64_t pivot = (L + R) >> 1;
-        if (cmp_plain(T, n, sa_at<IdxT>(d.sa, (uint64_t)pivot), a.tq, a0, m) < 0)
-            R = pivot;
+    const uint64_t first = lo;
+    // Upper bound: the first rank whose suffix's m-prefix is above P.
+    hi = n;
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (cmp_plain(T, n, sa_at<IdxT>(d.sa, mid), a.tq, a0, m) != CMP_LESS)
+            lo = mid + 1;
         else
-            L = pivot;
+            hi = mid;
     }
-    const int64_t RB = L;
-    write_result(a.out, q, (uint64_t)LB, (uint64_t)(RB + 1));
+    store_result(a.out, q, first, lo, a.trunc_cap);
 }
 
 __global__ void search_status_kernel(const int *flags, int *dst) {
@@ -449,10 +424,40 @@ __global__ void capacity_status_kernel(const int *overflow, int *dst) {
     if (*overflow && *dst == SA_OK) *dst = SA_ERR_CAPACITY;
 }
 
+// Precedence of statuses across the chunks of one call: a wait that ran out,
+// then a byte that is not a base, then a bad reference id.
+__device__ __forceinline__ int status_rank(int st) {
+    return st == SA_ERR_TIMEOUT ? 3 : st == SA_ERR_BASE ? 2 : st == SA_ERR_ARG ? 1 : 0;
+}
+
+__global__ void fold_status_kernel(const int *flags, int *acc) {
+    int st = flags[1];
+    if (st == 0 && flags[0]) st = SA_ERR_BASE;
+    if (st == 0 && flags[3]) st = SA_ERR_ARG;
+    atomicMax(acc, status_rank(st));
+}
+
+__global__ void fold_final_kernel(const int *acc, bool check_overflow, int *dst) {
+    const int rank = acc[0];
+    int st = rank == 3 ? SA_ERR_TIMEOUT : rank == 2 ? SA_ERR_BASE : rank == 1 ? SA_ERR_ARG : SA_OK;
+    if (st == SA_OK && check_overflow && acc[1]) st = SA_ERR_CAPACITY;
+    *dst = st;
+}
+
 }  // namespace
 
 cudaError_t launch_search_status(const int *flags, int *dst, cudaStream_t s) {
     search_status_kernel<<<1, 1, 0, s>>>(flags, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold_status(const int *flags, int *acc, cudaStream_t s) {
+    fold_status_kernel<<<1, 1, 0, s>>>(flags, acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold_final(const int *acc, bool check_overflow, int *dst, cudaStream_t s) {
+    fold_final_kernel<<<1, 1, 0, s>>>(acc, check_overflow, dst);
     return cudaGetLastError();
 }
 
@@ -465,21 +470,14 @@ cudaError_t launch_search(const SearchLaunch &L, cudaStream_t s) {
     if (L.n_q == 0) return cudaSuccess;
     const size_t smem = L.smem_bytes;
     const bool single = L.n_refs == 1 && L.q_ref == nullptr;
-    const uint32_t resident = L.threads * (L.blocks / (uint32_t)device_sm_count());
     auto go = [&](auto kernel) {
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kernel<<<L.blocks, L.threads, smem, s>>>(L);
     };
-    // The register cap follows the threads resident per SM.
     auto pick = [&](auto idx_tag, auto single_tag) {
         using I = decltype(idx_tag);
         constexpr bool S = decltype(single_tag)::value;
-        if (L.threads <= 256 && resident > 1536)
-            go(search_kernel<I, S, 8>);
-        else if (L.threads <= 512 && resident > 1024)
-            go(search_kernel<I, S, 3>);
-        else
-            go(search_kernel<I, S, 1>);
+        go(search_kernel<I, S>);
     };
     if (L.width == 4)
         single ? pick(uint32_t{}, std::true_type{}) : pick(uint32_t{}, std::false_type{});

@@ -38,7 +38,13 @@ SA_BUILD_HOST = 0x8
 SA_PARAM_Q_RANGE = 0x1
 SA_PARAM_REVERSE_COMPLEMENT = 0x2
 SA_PARAM_EXPIRE_WAITS = 0x4
+SA_PARAM_KMER_ORDER = 0x8
+SA_PARAM_INPUT_ORDER = 0x10
 SA_LOCATE_NOALLOC_MAX_QUERIES = 1 << 26
+SA_RESULT_INVALID = 0x1
+SA_RESULT_TRUNCATED = 0x2
+# int64 fields of one result: lo, hi, count, flags (32 bytes)
+RESULT_FIELDS = 4
 
 _u64 = ctypes.c_uint64
 _u32 = ctypes.c_uint32
@@ -52,7 +58,7 @@ class SAError(RuntimeError):
 
 
 class sa_result(ctypes.Structure):
-    _fields_ = [("lo", _u64), ("hi", _u64), ("count", _u64)]
+    _fields_ = [("lo", _u64), ("hi", _u64), ("count", _u64), ("flags", _u64)]
 
 
 class sa_search_params(ctypes.Structure):
@@ -84,6 +90,10 @@ SIGNATURES = {
     "sa_random_read_rate": (ctypes.c_int, [_u64, _u32, _u32, ctypes.POINTER(ctypes.c_double), _vp]),
     "sa_random_read_rate_ex": (ctypes.c_int, [_u64, _u32, _u32, _u32, ctypes.POINTER(ctypes.c_double), _vp]),
     "sa_suffix_array_host": (ctypes.c_int, [_vp, _u64, _u32, _vp]),
+    "sa_search_order": (ctypes.c_int, [ctypes.POINTER(_vp), _u32, _u64, ctypes.POINTER(sa_search_params),
+                                       ctypes.POINTER(ctypes.c_int)]),
+    "sa_scratch_info": (ctypes.c_int, [ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64),
+                                       ctypes.c_int]),
 }
 
 _lib = None
@@ -239,7 +249,32 @@ def _refs(refs) -> tuple:
 
 def _out_like(n_q: int, like):
     dev = like.device if torch is not None and isinstance(like, torch.Tensor) else "cpu"
-    return torch.empty((n_q, 3), dtype=torch.int64, device=dev)
+    return torch.empty((n_q, RESULT_FIELDS), dtype=torch.int64, device=dev)
+
+
+def _nbytes(x) -> int:
+    if torch is not None and isinstance(x, torch.Tensor):
+        return x.numel() * x.element_size()
+    if isinstance(x, np.ndarray):
+        return x.nbytes
+    raise TypeError(f"unsupported buffer type {type(x)!r}")
+
+
+def _check_results_buffer(out, n_q: int, what: str):
+    """Results are 32 bytes each (lo, hi, count, flags): a smaller buffer
+    would be written past its end, so it is refused here."""
+    if _nbytes(out) < n_q * ctypes.sizeof(sa_result):
+        raise ValueError(f"{what}: results buffer holds {_nbytes(out)} bytes, "
+                         f"{n_q} results need {n_q * ctypes.sizeof(sa_result)} (shape (n_q, {RESULT_FIELDS}) int64)")
+
+
+def _check_locate_buffers(out_offsets, out_pos, n_q: int, capacity: int, width: int, what: str):
+    """Offsets take n_q + 1 int64; positions capacity entries of the suffix array's width."""
+    if _nbytes(out_offsets) < (n_q + 1) * 8:
+        raise ValueError(f"{what}: out_offsets holds {_nbytes(out_offsets)} bytes, needs {(n_q + 1) * 8}")
+    if out_pos is not None and _nbytes(out_pos) < capacity * width:
+        raise ValueError(f"{what}: out_pos holds {_nbytes(out_pos)} bytes, capacity {capacity} needs "
+                         f"{capacity * width}")
 
 
 def _search(fn, refs, q_bases, q_offsets, q_ref, out, stream, params=None):
@@ -247,6 +282,7 @@ def _search(fn, refs, q_bases, q_offsets, q_ref, out, stream, params=None):
     n_q = int((q_offsets.numel() if isinstance(q_offsets, torch.Tensor) else len(q_offsets)) - 1)
     if out is None:
         out = _out_like(n_q, q_offsets)
+    _check_results_buffer(out, n_q, fn.__name__)
     args = [arr, nr, _ptr(q_bases), _ptr(q_offsets), _ptr(q_ref), n_q, _ptr(out), _stream(stream)]
     if params is not None:
         args.append(ctypes.byref(params))
@@ -255,7 +291,8 @@ def _search(fn, refs, q_bases, q_offsets, q_ref, out, stream, params=None):
 
 
 def sa_search_batch(refs, q_bases, q_offsets, q_ref=None, out=None, stream=None, params=None):
-    """[lo, hi, count] per query, int64 tensor of shape (n_q, 3); -1 marks an invalid query."""
+    """[lo, hi, count, flags] per query, int64 tensor of shape (n_q, 4); lo = hi =
+    count = -1 and flags = SA_RESULT_INVALID mark an invalid query."""
     if params is not None:
         return _search(lib().sa_search_batch_ex, refs, q_bases, q_offsets, q_ref, out, stream, params)
     return _search(lib().sa_search_batch, refs, q_bases, q_offsets, q_ref, out, stream)
@@ -273,6 +310,7 @@ def sa_locate(refs, res, cap: int, q_ref=None, out_offsets=None, out_pos=None, c
     exactly the needed size is allocated on the results' device."""
     arr, nr = _refs(refs)
     n_q = int(res.shape[0])
+    _check_results_buffer(res, n_q, "sa_locate")
     dev = res.device if isinstance(res, torch.Tensor) else "cpu"
     dt = torch.int32 if (refs if isinstance(refs, Index) else refs[0]).width == 4 else torch.int64
     if out_offsets is None:
@@ -286,6 +324,7 @@ def sa_locate(refs, res, cap: int, q_ref=None, out_offsets=None, out_pos=None, c
         capacity = total
     if capacity is None:
         capacity = int(out_pos.numel() if isinstance(out_pos, torch.Tensor) else out_pos.size)
+    _check_locate_buffers(out_offsets, out_pos, n_q, capacity, 4 if dt == torch.int32 else 8, "sa_locate")
     _check(lib().sa_locate(arr, nr, _ptr(q_ref), _ptr(res), n_q, cap, _ptr(out_offsets), _ptr(out_pos), capacity, s),
            "sa_locate")
     return out_offsets, out_pos
@@ -309,6 +348,8 @@ def sa_search_locate(refs, q_bases, q_offsets, cap: int, q_ref=None, out=None, o
         out_pos = torch.empty(max(capacity, 1), dtype=dt, device=dev)
     if capacity is None:
         capacity = int(out_pos.numel() if isinstance(out_pos, torch.Tensor) else out_pos.size)
+    _check_results_buffer(out, n_q, "sa_search_locate")
+    _check_locate_buffers(out_offsets, out_pos, n_q, capacity, 4 if dt == torch.int32 else 8, "sa_search_locate")
     p = params if params is not None else sa_search_params()
     _check(lib().sa_search_locate(arr, nr, _ptr(q_bases), _ptr(q_offsets), _ptr(q_ref), n_q, _ptr(out), cap,
                                   _ptr(out_offsets), _ptr(out_pos), capacity, _stream(stream), ctypes.byref(p)),
@@ -335,3 +376,21 @@ def sa_suffix_array_host(text, width: int = 32) -> np.ndarray:
     out = np.empty(max(n, 1), dtype=np.uint32 if width == 32 else np.uint64)
     _check(lib().sa_suffix_array_host(_ptr(text), n, width // 8, _ptr(out)), "sa_suffix_array_host")
     return out[:n]
+
+
+def sa_scratch_info(reset_high: bool = False) -> dict:
+    """The library's scratch pool on the current device: bytes reserved, bytes
+    in use, and the high-water mark of use (optionally reset)."""
+    r, u, h = _u64(), _u64(), _u64()
+    _check(lib().sa_scratch_info(ctypes.byref(r), ctypes.byref(u), ctypes.byref(h), int(reset_high)),
+           "sa_scratch_info")
+    return {"reserved": r.value, "used": u.value, "used_high": h.value}
+
+
+def sa_search_order(refs, n_q: int, params=None) -> str:
+    """'kmer' if a search of n_q queries over refs would run in k-mer order, else 'input'."""
+    arr, nr = _refs(refs)
+    v = ctypes.c_int(0)
+    _check(lib().sa_search_order(arr, nr, n_q, None if params is None else ctypes.byref(params), ctypes.byref(v)),
+           "sa_search_order")
+    return "kmer" if v.value else "input"

@@ -35,7 +35,7 @@ class Request:
     offsets: np.ndarray   # int64, n + 1 offsets starting at 0
     arrival: float        # seconds since the start of the trace
     cap: int = 0          # positions to locate per query (0: counts only)
-    results: Optional[np.ndarray] = None   # (n, 3) int64: lo, hi, count
+    results: Optional[np.ndarray] = None   # (n, 4) int64: lo, hi, count, flags
     pos_offsets: Optional[np.ndarray] = None  # (n + 1) int64 when cap > 0
     positions: Optional[np.ndarray] = None    # located positions, suffix-array order per query
     done: float = math.nan
@@ -99,10 +99,10 @@ class _Slot:
         self.bases = torch.empty(max(1, max_bases), dtype=torch.uint8, device=device)
         self.offsets = torch.empty(max_q + 1, dtype=torch.int64, device=device)
         self.qref = torch.empty(max(1, max_q), dtype=torch.int32, device=device)
-        self.out = torch.empty((max(1, max_q), 3), dtype=torch.int64, device=device)
+        self.out = torch.empty((max(1, max_q), sa.RESULT_FIELDS), dtype=torch.int64, device=device)
         self.h_offsets = torch.empty(max_q + 1, dtype=torch.int64).pin_memory()
         self.h_qref = torch.empty(max(1, max_q), dtype=torch.int32).pin_memory()
-        self.h_out = torch.empty((max(1, max_q), 3), dtype=torch.int64).pin_memory()
+        self.h_out = torch.empty((max(1, max_q), sa.RESULT_FIELDS), dtype=torch.int64).pin_memory()
         # located positions (when the server locates): every query's first max_cap
         self.pos_cap = max(1, max_q * max_cap)
         self.loc_offs = torch.empty(max_q + 1, dtype=torch.int64, device=device) if max_cap else None
@@ -205,6 +205,11 @@ class Server:
         q = 0
         for r in slot.requests:
             r.results = out[q:q + r.n].copy()
+            # the batch was located up to its largest cap: truncation is per
+            # request, and only a request that asked for positions has it
+            valid = r.results[:, 0] != -1
+            trunc = (r.results[:, 2] > r.cap) if r.cap else np.zeros(r.n, dtype=bool)
+            r.results[:, 3] = np.where(valid, np.where(trunc, sa.SA_RESULT_TRUNCATED, 0), sa.SA_RESULT_INVALID)
             if r.cap:
                 r.pos_offsets, r.positions = split_positions(r.results, offs[q:q + r.n + 1], pos, slot.cap, r.cap)
             r.done = now

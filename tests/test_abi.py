@@ -65,5 +65,5 @@ def test_host_side_argument_checks(salib):
 
 
 def test_result_struct_layout(salib):
-    assert ctypes.sizeof(salib.sa_result) == 24
+    assert ctypes.sizeof(salib.sa_result) == 32  # one DRAM sector per result
     assert ctypes.sizeof(salib.sa_search_params) == 72

@@ -30,8 +30,12 @@ def env():
 
 
 def _alone(sa, idx, r):
+    """The request run by itself: a search, with its own locate cap if it asked for positions."""
     bases = r.bases[:r.nbases].cuda() if r.nbases else torch.zeros(1, dtype=torch.uint8, device="cuda")
-    return sa.sa_search_batch(idx, bases, torch.from_numpy(r.offsets).cuda()).cpu().numpy()
+    offs = torch.from_numpy(r.offsets).cuda()
+    if r.cap:
+        return sa.sa_search_locate(idx, bases, offs, r.cap)[0].cpu().numpy()
+    return sa.sa_search_batch(idx, bases, offs).cpu().numpy()
 
 
 def test_serving_results_equal_alone_and_oracle(env):
@@ -116,7 +120,7 @@ def test_cuda_graph_capture_and_replay(env):
     qb2, _, _ = datagen.queries(ref, n_q, 402, m=90, frac_sampled=0.8, subs=(0, 1))
     bases = torch.from_numpy(qb1).cuda()
     offs = torch.from_numpy(qo).cuda()
-    out = torch.empty((n_q, 3), dtype=torch.int64, device="cuda")
+    out = torch.empty((n_q, sa.RESULT_FIELDS), dtype=torch.int64, device="cuda")
     loc_off = torch.empty(n_q + 1, dtype=torch.int64, device="cuda")
     loc_pos = torch.empty(n_q * 8, dtype=torch.int32, device="cuda")
     p = sa.sa_search_params()

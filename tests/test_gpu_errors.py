@@ -50,12 +50,12 @@ def test_expired_wait_reports_timeout(sa, case):
     qb_d, qo_d = torch.from_numpy(qb).cuda(), torch.from_numpy(qo).cuda()
     st = _status_word()
     p = sa.sa_search_params(flags=sa.SA_PARAM_EXPIRE_WAITS, device_status=st.data_ptr())
-    out = torch.empty((qo.size - 1, 3), dtype=torch.int64, device="cuda")
+    out = torch.empty((qo.size - 1, sa.RESULT_FIELDS), dtype=torch.int64, device="cuda")
     sa.sa_search_batch(idx, qb_d, qo_d, out=out, params=p)  # device output: queued, returns OK
     torch.cuda.synchronize()
     assert int(st.item()) == sa.SA_ERR_TIMEOUT
     with pytest.raises(sa.SAError) as e:  # host output: the call returns the status itself
-        sa.sa_search_batch(idx, qb, qo, out=np.empty((qo.size - 1, 3), dtype=np.int64),
+        sa.sa_search_batch(idx, qb, qo, out=np.empty((qo.size - 1, sa.RESULT_FIELDS), dtype=np.int64),
                            params=sa.sa_search_params(flags=sa.SA_PARAM_EXPIRE_WAITS))
     assert e.value.status == sa.SA_ERR_TIMEOUT
     # the context is still usable and the next call is right
@@ -110,6 +110,9 @@ def test_capacity_errors(sa, case):
         torch.cuda.synchronize()
         assert int(st.item()) == want
         assert int(offs[-1].item()) == need
+        # each result carries SA_RESULT_TRUNCATED exactly when count > cap
+        r = res.cpu().numpy()
+        assert np.array_equal(r[:, 3], np.where(r[:, 2] > cap, sa.SA_RESULT_TRUNCATED, 0))
     # separate locate with host offsets: the total is read back, so the call reports it
     res = sa.sa_search_batch(idx, qb_d, qo_d)
     offs_h = np.empty(n_q + 1, dtype=np.int64)

@@ -53,7 +53,9 @@ def test_search_and_locate_full_size(c2):
     assert np.array_equal(pos.cpu().numpy().astype(np.int64), osa[starts + within])
     # the one-call path that the benchmark times gives the same results and positions
     res2, offs2, pos2 = sa.sa_search_locate(idx, qb, qo, w.cap)
-    assert torch.equal(res2, res)
+    assert torch.equal(res2[:, :3], res[:, :3])
+    # the one call marks each query whose count exceeds the cap as truncated
+    assert np.array_equal(res2[:, 3].cpu().numpy(), np.where(got[:, 2] > w.cap, sa.SA_RESULT_TRUNCATED, 0))
     assert np.array_equal(offs2.cpu().numpy(), offs)
     assert torch.equal(pos2[:int(offs[-1])].cpu(), pos[:int(offs[-1])].cpu())
     # every exact copy from the reference occurs; counts agree with brute force on a sample

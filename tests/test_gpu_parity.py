@@ -62,7 +62,7 @@ def test_paper_example(sa, golden):
     qb, qo = _batch(qs)
     got = sa.sa_search_batch(idx, _dev(qb), _dev(qo)).cpu().tolist()
     for (q, lb, rb), g in zip(golden["search"], got):
-        assert g == [int(lb), int(rb) + 1, int(rb) - int(lb) + 1], q
+        assert g[:3] == [int(lb), int(rb) + 1, int(rb) - int(lb) + 1], q
     offs, pos = sa.sa_locate(idx, sa.sa_search_batch(idx, _dev(qb), _dev(qo)), 8)
     a = qs.index("a")
     assert pos[offs[a]:offs[a + 1]].cpu().tolist() == [int(p) for p in golden["positions"][0][1:]]
@@ -183,12 +183,12 @@ def test_host_buffers_match_device_buffers(sa):
     assert torch.equal(idx_d.suffix_array().cpu(), idx_h.suffix_array().cpu())
     qb, qo, _ = datagen.queries(ref, 3000, 22, m=(10, 200), frac_sampled=0.7, subs=(0, 1))
     r_dev = sa.sa_search_batch(idx_d, _dev(qb), _dev(qo)).cpu()
-    out_host = torch.empty((qo.size - 1, 3), dtype=torch.int64)
+    out_host = torch.empty((qo.size - 1, sa.RESULT_FIELDS), dtype=torch.int64)
     r_host = sa.sa_search_batch(idx_d, qb, qo, out=out_host)
     assert torch.equal(r_dev, r_host)
     pinned = torch.from_numpy(qb).pin_memory()
     r_pin = sa.sa_search_batch(idx_d, pinned, torch.from_numpy(qo).pin_memory(),
-                               out=torch.empty((qo.size - 1, 3), dtype=torch.int64).pin_memory())
+                               out=torch.empty((qo.size - 1, sa.RESULT_FIELDS), dtype=torch.int64).pin_memory())
     torch.cuda.synchronize()
     assert torch.equal(r_dev, r_pin)
     offs_d, pos_d = sa.sa_locate(idx_d, r_dev.to(DEV), 16)
@@ -247,20 +247,20 @@ def test_errors(sa):
     idx = sa.sa_build(_dev(np.frombuffer(b"ACGTACGT", dtype=np.uint8)))
     qb, qo = _batch(["ACG", "AXG"])
     with pytest.raises(sa.SAError) as e:
-        sa.sa_search_batch(idx, qb, qo, out=torch.empty((2, 3), dtype=torch.int64))
+        sa.sa_search_batch(idx, qb, qo, out=torch.empty((2, sa.RESULT_FIELDS), dtype=torch.int64))
     assert e.value.status == sa.SA_ERR_BASE
     # on the device only the query with the bad byte is marked invalid
     got = sa.sa_search_batch(idx, _dev(qb), _dev(qo)).cpu()
-    assert got[0].tolist() == [0, 2, 2] and (got[1] == -1).all()
+    assert got[0].tolist() == [0, 2, 2, 0] and (got[1][:3] == -1).all() and got[1][3] == sa.SA_RESULT_INVALID
     got = sa.sa_search_batch_plain(idx, _dev(qb), _dev(qo)).cpu()
-    assert got[0].tolist() == [0, 2, 2] and (got[1] == -1).all()
+    assert got[0].tolist() == [0, 2, 2, 0] and (got[1][:3] == -1).all() and got[1][3] == sa.SA_RESULT_INVALID
     # out-of-range reference id
     qb, qo = _batch(["ACG", "CG"])
     got = sa.sa_search_batch([idx, idx], _dev(qb), _dev(qo), q_ref=_dev(np.array([0, 2], dtype=np.uint32))).cpu()
-    assert got[0].tolist() == [0, 2, 2] and (got[1] == -1).all()
+    assert got[0].tolist() == [0, 2, 2, 0] and (got[1][:3] == -1).all() and got[1][3] == sa.SA_RESULT_INVALID
     with pytest.raises(sa.SAError) as e:
         sa.sa_search_batch([idx, idx], qb, qo, q_ref=np.array([0, 2], dtype=np.uint32),
-                           out=torch.empty((2, 3), dtype=torch.int64))
+                           out=torch.empty((2, sa.RESULT_FIELDS), dtype=torch.int64))
     assert e.value.status == sa.SA_ERR_ARG
     # two references of different widths in one call
     idx64 = sa.sa_build(_dev(np.frombuffer(b"ACGTACGT", dtype=np.uint8)), width=64)

@@ -17,19 +17,20 @@ SRC = os.path.join(ROOT, "oracle", "oracle.c")
 MUTATIONS = {
     # proper prefix sorts after the longer suffix (Table I / reading R3)
     "prefix_last": ("return li < lj ? -1 : 1;", "return li < lj ? 1 : -1;"),
-    # Alg. 1 LB test made strict
-    "lb_strict": ("if (query_cmp(T, n, sa[pivot], P, m, NULL) <= 0)",
-                  "if (query_cmp(T, n, sa[pivot], P, m, NULL) < 0)"),
-    # RB taken from the wrong boundary
-    "rb_from_R": ("int64_t RB = L;", "int64_t RB = R;"),
+    # lower-bound test made strict (reading R1)
+    "lb_strict": ("if (query_cmp(T, n, sa[mid], P, m, NULL) > 0)",
+                  "if (query_cmp(T, n, sa[mid], P, m, NULL) >= 0)"),
+    # upper-bound test loses its equality case, so hi stops at lo (reading R1)
+    "ub_strict": ("if (query_cmp(T, n, sa[mid], P, m, NULL) >= 0)",
+                  "if (query_cmp(T, n, sa[mid], P, m, NULL) > 0)"),
     # a suffix that ends early compares larger than the query
     "short_suffix_big": ("            return 1;\n        }\n        if (T[p + k] != P[k]) {",
                          "            return -1;\n        }\n        if (T[p + k] != P[k]) {"),
     # mismatch direction flipped
     "mismatch_sign": ("return P[k] < T[p + k] ? -1 : 1;", "return P[k] < T[p + k] ? 1 : -1;"),
-    # boundaries start at L = 0 (reading R2)
-    "left_zero": ("    int64_t L = -1, R = n;\n    while (R > L + 1) {\n        int64_t pivot = (L + R) >> 1;\n        if (query_cmp(T, n, sa[pivot], P, m, NULL) <= 0)",
-                  "    int64_t L = 0, R = n;\n    while (R > L + 1) {\n        int64_t pivot = (L + R) >> 1;\n        if (query_cmp(T, n, sa[pivot], P, m, NULL) <= 0)"),
+    # the search range leaves out rank 0 (reading R2)
+    "left_zero": ("int64_t a = 0, b = n; /* the lower bound lies in [a, b] */",
+                  "int64_t a = 1, b = n; /* the lower bound lies in [a, b] */"),
     # comparator skips the first base
     "skip_first_base": ("for (int64_t t = 0; t < k; t++) {", "for (int64_t t = 1; t < k; t++) {"),
 }

@@ -4,8 +4,10 @@ Some callers cannot call cudaMalloc -- their device memory is owned up front
 by another allocator, or they run a latency-critical loop where an allocation
 could block or fail.  sa_locate_noalloc keeps its scan scratch in a static
 device array instead.  This test calls it through the C ABI twice in a row
-(the array keeps the previous call's contents) and requires both results to
-equal sa_locate's exactly, the tolerance of every integer test here.  The file
+(the array keeps the previous call's contents), requires both results to
+equal sa_locate's exactly, the tolerance of every integer test here, and
+checks around each call that nothing was allocated: the library's scratch
+pool, torch's allocator and the device's free memory are unchanged.  The file
 is named to be collected last."""
 import ctypes
 
@@ -53,8 +55,20 @@ def test_noalloc_matches_sa_locate_twice(sa, width):
         for call in range(2):
             offs = torch.full((n_q + 1,), -7, dtype=torch.int64, device="cuda")
             pos = torch.full((max(total, 1),), -7, dtype=dt, device="cuda")
+            # the call must allocate nothing: the library's scratch pool sees no
+            # allocation (its high-water mark stays 0 after a reset), torch's
+            # allocator and the device's free memory do not change
+            torch.cuda.synchronize()
+            before = sa.sa_scratch_info(reset_high=True)
+            torch_before = torch.cuda.memory_allocated()
+            free_before = torch.cuda.mem_get_info()[0]
             assert _noalloc(sa, idxs, res, cap, qref_d, offs, pos, total) == sa.SA_OK
             torch.cuda.synchronize()
+            after = sa.sa_scratch_info()
+            assert after["used_high"] == 0 and after["used"] == 0, (before, after)
+            assert after["reserved"] == before["reserved"]
+            assert torch.cuda.memory_allocated() == torch_before
+            assert torch.cuda.mem_get_info()[0] == free_before
             assert torch.equal(offs, offs_ref), (cap, call)
             assert torch.equal(pos[:total], pos_ref[:total]), (cap, call)
 
@@ -62,7 +76,7 @@ def test_noalloc_matches_sa_locate_twice(sa, width):
 def test_noalloc_rejects_too_many_queries_and_host_buffers(sa):
     ref = datagen.reference(5000, 3)
     idx = sa.sa_build(torch.from_numpy(ref).cuda())
-    res = torch.zeros((4, 3), dtype=torch.int64, device="cuda")
+    res = torch.zeros((4, sa.RESULT_FIELDS), dtype=torch.int64, device="cuda")
     offs = torch.zeros(5, dtype=torch.int64, device="cuda")
     arr = (ctypes.c_void_p * 1)(idx.handle.value)
     L = sa.lib()
