@@ -644,6 +644,9 @@ def run_human_sized(args, world, rank, local):
     plain_qps = n_plain / (min(plain_ms) / 1e3)
     del qb_d
     torch.cuda.empty_cache()
+    serving = None
+    if args.serve_seconds > 0 and world == 1:
+        serving = serve_on_index([idx], w.q_bases, w.q_offsets, args.serve_seconds)
 
     line = None
     if rank == 0:
@@ -701,6 +704,7 @@ def run_human_sized(args, world, rank, local):
                     "upload_bound_ms": h2d / (h2d_gbs * 1e9) * 1e3},
             "gpu_launches": args.steps * launches,
             "search_order": order,
+            "serving": serving,
             "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clocks,
@@ -709,6 +713,40 @@ def run_human_sized(args, world, rank, local):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def serve_on_index(idxs, q_bases, q_offsets, seconds: float, rate: float = 2000.0, pool: int = 2_000_000,
+                   caps=(0, 16)):
+    """Serving on resident indexes: a Poisson trace (`rate` requests/s for
+    `seconds`), each request a log-uniform 1-100,000 queries sliced from a
+    pool of the workload's queries, with a locate cap drawn from `caps`;
+    served by the continuous-batching server, by one optimized call per
+    request, and by one call of the plain Alg. 1 kernel per request."""
+    import torch
+
+    from paper_1303_3692_gb300 import serve
+
+    n = min(pool, q_offsets.size - 1)
+    qo = np.ascontiguousarray(q_offsets[:n + 1])
+    pools = [(torch.from_numpy(np.ascontiguousarray(q_bases[:int(qo[-1])])).pin_memory(), qo)]
+    max_cap = max(caps)
+    warm = serve.make_trace(pools, rate=rate, duration=0.2, seed=1, caps=caps)
+    serve.Server(idxs, slots=3, max_cap=max_cap).run(warm)
+    out = {"trace": {"rate_per_s": rate, "seconds": seconds, "queries_per_request": "log-uniform 1-100000",
+                     "caps": list(caps)}}
+    trace = serve.make_trace(pools, rate=rate, duration=seconds, seed=2, caps=caps)
+    out["batched"] = serve.Server(idxs, slots=3, max_cap=max_cap).run(trace)
+    for kernel in ("optimized", "plain"):
+        t = serve.make_trace(pools, rate=rate, duration=seconds, seed=2, caps=caps)
+        serve.run_plain(idxs, t[:2], kernel=kernel)  # warm
+        t = serve.make_trace(pools, rate=rate, duration=seconds, seed=2, caps=caps)
+        out[f"per_request_{kernel}"] = serve.run_plain(idxs, t, kernel=kernel)
+    b = out["batched"]
+    for kernel in ("optimized", "plain"):
+        o = out[f"per_request_{kernel}"]
+        out[f"p99_gain_vs_{kernel}"] = o["p99_ms"] / b["p99_ms"] if b["p99_ms"] else None
+        out[f"p50_gain_vs_{kernel}"] = o["p50_ms"] / b["p50_ms"] if b["p50_ms"] else None
+    return out
 
 
 # DRAM bytes (read + write) per launch of the 3.1 Gbp search phase from one ncu

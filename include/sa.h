@@ -158,6 +158,13 @@ typedef struct sa_search_params {
  * in flight all at once whatever its order. */
 #define SA_PARAM_KMER_ORDER 0x8u
 #define SA_PARAM_INPUT_ORDER 0x10u
+/* sa_search_params.flags: each query names its strand -- bit 31 of q_ref[q]
+ * set means search query q's reverse complement (as SA_PARAM_REVERSE_COMPLEMENT
+ * does for a whole batch); the reference id is q_ref[q] & 0x7FFFFFFF.  q_ref
+ * is then required, also with one index (ids 0), and the batch is packed in
+ * both directions (twice the packed batch's scratch).  Not together with
+ * SA_PARAM_REVERSE_COMPLEMENT (SA_ERR_ARG).  sa_locate ignores bit 31 of q_ref. */
+#define SA_PARAM_STRAND_PER_QUERY 0x20u
 
 /*
  * sa_build -- index one reference (Section III).

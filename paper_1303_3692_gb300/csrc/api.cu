@@ -250,10 +250,15 @@ int search_device(const sa_index *const *refs, uint32_t n_refs, uint32_t width, 
     if (threads < 32 || threads > 1024 || threads % 32 || bps == 0 || threads * bps > 2048) return SA_ERR_ARG;
     if (threads * bps > 1024) bps = 1024 / threads;  // the persistent kernel takes 64 registers a thread
     if (params && params->front_probes > 64) return SA_ERR_ARG;
+    const bool strand_bits = params && (params->flags & SA_PARAM_STRAND_PER_QUERY);
+    const bool revcomp = params && (params->flags & SA_PARAM_REVERSE_COMPLEMENT);
+    if (strand_bits && (revcomp || !q_ref)) return SA_ERR_ARG;
     cudaError_t err = cudaSuccess;
     const uint64_t nwords = (total + 31) / 32;
-    uint64_t *tq = sc.get<uint64_t>(nwords + SA_TQ_PAD_WORDS);
-    uint32_t *tv = sc.get<uint32_t>(nwords + SA_TQ_PAD_WORDS);
+    // both packings, one after the other, when each query names its strand
+    const uint64_t tq_words = (nwords + SA_TQ_PAD_WORDS) * (strand_bits ? 2 : 1);
+    uint64_t *tq = sc.get<uint64_t>(tq_words);
+    uint32_t *tv = sc.get<uint32_t>(tq_words);
     uint4 *wrec = plain ? nullptr : sc.get<uint4>(4 * n_q);
     uint64_t ktotal = 0;
     for (uint32_t r = 0; r < n_refs; r++)
@@ -307,7 +312,9 @@ int search_device(const sa_index *const *refs, uint32_t n_refs, uint32_t width, 
     // and the first pass does best with three probes (measured)
     L.front_probes = params && params->front_probes ? params->front_probes
                                                     : (kmer_order ? 3u : default_front_probes(refs, n_refs));
-    L.revcomp = params && (params->flags & SA_PARAM_REVERSE_COMPLEMENT);
+    L.revcomp = revcomp;
+    L.strand_bits = strand_bits;
+    L.rc_base = strand_bits ? (nwords + SA_TQ_PAD_WORDS) * 32 : 0;
     L.expire_waits = params && (params->flags & SA_PARAM_EXPIRE_WAITS);
     L.trunc_cap = trunc_cap;
     L.ktotal = ktotal;

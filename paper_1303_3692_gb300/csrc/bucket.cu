@@ -27,8 +27,9 @@
 //   bucket_scatter_kernel  per tile of queries, each bucket's run reserved at
 //                          once and every query's 64-byte record (length,
 //                          index, reference, first base in the packed batch,
-//                          first 128 bases) written at its slot, flagged when
-//                          it has a k-mer bracket to read.
+//                          first 128 bases; flagged when it has a k-mer
+//                          bracket to read) put at its slot, through shared
+//                          memory so that the runs are stored coalesced.
 // The first pass and then the persistent kernel of search.cu take the queries
 // in that order, so the reads in flight at any time stay in a few slices.
 #include "sa_internal.cuh"
@@ -48,22 +49,20 @@ struct BucketRef {
     uint32_t kmer_k;  // 0: no k-mer table
 };
 
-// The query's range in the packed batch (mirrored for the other strand) and
-// whether the range and the reference id are usable.
-__device__ __forceinline__ bool query_range(const SearchLaunch &a, uint64_t q, uint32_t r, uint64_t *qa_out,
+// The query's first base in the packed batch (in the reverse-complement
+// packing for the other strand), its length, its reference id (*r, the strand
+// bit cleared) and whether the range and the reference id are usable.
+__device__ __forceinline__ bool query_range(const SearchLaunch &a, uint64_t q, uint32_t *r, uint64_t *qa_out,
                                             uint32_t *m_out, bool *bad_range, bool *bad_ref) {
-    uint64_t qa = __ldg(a.q_off + q) - a.first, qe = __ldg(a.q_off + q + 1) - a.first;
+    const uint64_t qa = __ldg(a.q_off + q) - a.first, qe = __ldg(a.q_off + q + 1) - a.first;
+    const bool rc = a.revcomp || (a.strand_bits && (*r & kStrandBit));
+    if (a.strand_bits) *r &= ~kStrandBit;
     const bool range_ok = qa <= qe && qe <= a.total && qe - qa < (1ull << 31);
     *bad_range = !range_ok;
-    *bad_ref = range_ok && r >= a.n_refs;
-    if (range_ok && a.revcomp) {  // the reverse complement sits at the mirrored range
-        const uint64_t t = a.total - qe;
-        qe = a.total - qa;
-        qa = t;
-    }
-    *qa_out = qa;
+    *bad_ref = range_ok && *r >= a.n_refs;
+    *qa_out = range_ok ? strand_start(qa, qe, a.total, rc, a.rc_base) : qa;
     *m_out = range_ok ? (uint32_t)(qe - qa) : 0u;
-    return range_ok && r < a.n_refs;
+    return range_ok && *r < a.n_refs;
 }
 
 template <bool kSingle>
@@ -82,11 +81,11 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_count_kernel(const __gr
     for (int it = 0; it < kBucketItems; it++) {
         const uint64_t q = tile + (uint64_t)it * kBucketThreads + threadIdx.x;
         if (q >= a.n_q) break;
-        const uint32_t r = kSingle ? 0u : __ldg(a.q_ref + q);
+        uint32_t r = kSingle ? 0u : __ldg(a.q_ref + q);
         uint64_t qa;
         uint32_t m;
         bool bad_range, bad_ref;
-        bool ok = query_range(a, q, r, &qa, &m, &bad_range, &bad_ref);
+        bool ok = query_range(a, q, &r, &qa, &m, &bad_range, &bad_ref);
         any_bad |= bad_range;
         any_bad_ref |= bad_ref;
         uint64_t w[4];
@@ -138,47 +137,91 @@ __global__ void bucket_scan_kernel(const __grid_constant__ SearchLaunch a) {
     if (lane == 0) *a.wl_in_count = carry;
 }
 
+// Scatter: one CTA per tile of kScatterTile queries.  The tile's records are
+// first built in shared memory in bucket order (each bucket's run of the
+// tile contiguous), then copied out run by run: consecutive threads store
+// consecutive 16-byte words of a run, so the stores coalesce (a record
+// written straight to its slot from each lane would put the 32 lanes of a
+// warp in 32 different runs).
+constexpr int kScatterThreads = 256;
+constexpr int kScatterItems = 4;
+constexpr uint32_t kScatterTile = (uint32_t)kScatterThreads * kScatterItems;  // 64 KB of records
+constexpr size_t kScatterSmem = (size_t)kScatterTile * 64;
+
 template <bool kSingle>
-__global__ void __launch_bounds__(kBucketThreads) bucket_scatter_kernel(const __grid_constant__ SearchLaunch a,
-                                                                       uint4 *__restrict__ list) {
+__global__ void __launch_bounds__(kScatterThreads) bucket_scatter_kernel(const __grid_constant__ SearchLaunch a,
+                                                                        uint4 *__restrict__ list) {
+    extern __shared__ uint4 srec[];  // kScatterTile records of 4 uint4
     __shared__ uint32_t cnt[kNumBuckets + 1];
+    __shared__ uint32_t off[kNumBuckets + 1];
     __shared__ uint32_t base[kNumBuckets + 1];
+    __shared__ uint16_t slot_bucket[kScatterTile];
+    __shared__ uint32_t n_valid;
     for (unsigned i = threadIdx.x; i <= kNumBuckets; i += blockDim.x) cnt[i] = 0;
     __syncthreads();
-    const uint64_t tile = (uint64_t)blockIdx.x * kBucketTile;
-    uint16_t b[kBucketItems];
-    uint32_t rank[kBucketItems];
+    const uint64_t tile = (uint64_t)blockIdx.x * kScatterTile;
+    uint16_t b[kScatterItems];
+    uint32_t rank[kScatterItems];
 #pragma unroll
-    for (int it = 0; it < kBucketItems; it++) {
-        const uint64_t q = tile + (uint64_t)it * kBucketThreads + threadIdx.x;
+    for (int it = 0; it < kScatterItems; it++) {
+        const uint64_t q = tile + (uint64_t)it * kScatterThreads + threadIdx.x;
         b[it] = q < a.n_q ? a.qbucket[q] : kNoQuery;
         rank[it] = b[it] != kNoQuery ? atomicAdd(&cnt[b[it]], 1u) : 0u;
     }
     __syncthreads();
-    // each bucket's run of this tile, reserved with one atomic
+    // the tile's runs: exclusive scan of its counts (first warp), and each
+    // run's place in the list, reserved with one atomic per bucket
+    if (threadIdx.x < 32) {
+        const unsigned lane = threadIdx.x;
+        uint32_t carry = 0;
+        for (unsigned s0 = 0; s0 <= kNumBuckets; s0 += 32) {
+            const unsigned i = s0 + lane;
+            const uint32_t v = i <= kNumBuckets ? cnt[i] : 0u;
+            uint32_t x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                if (lane >= (unsigned)o) x += y;
+            }
+            if (i <= kNumBuckets) off[i] = carry + x - v;
+            carry += __shfl_sync(0xFFFFFFFFu, x, 31);
+        }
+        if (lane == 0) n_valid = carry;
+    }
     for (unsigned i = threadIdx.x; i <= kNumBuckets; i += blockDim.x)
         base[i] = cnt[i] ? atomicAdd(a.bcursor + i, cnt[i]) : 0u;
     __syncthreads();
 #pragma unroll 1
-    for (int it = 0; it < kBucketItems; it++) {
+    for (int it = 0; it < kScatterItems; it++) {
         if (b[it] == kNoQuery) continue;
-        const uint64_t q = tile + (uint64_t)it * kBucketThreads + threadIdx.x;
-        const uint32_t r = kSingle ? 0u : __ldg(a.q_ref + q);
+        const uint64_t q = tile + (uint64_t)it * kScatterThreads + threadIdx.x;
+        uint32_t r = kSingle ? 0u : __ldg(a.q_ref + q);
         uint64_t qa;
         uint32_t m;
         bool bad_range, bad_ref;
-        query_range(a, q, r, &qa, &m, &bad_range, &bad_ref);
+        query_range(a, q, &r, &qa, &m, &bad_range, &bad_ref);
         uint64_t w[4];
         load_query_head(a.tq, a.tv, qa >> 5, (uint32_t)(qa & 31u), m, false, w);
         const bool entry = b[it] < kNumBuckets;
         const uint32_t n = (uint32_t)a.refs.r[kSingle ? 0u : r].n;
-        uint4 *dst = list + 4 * (size_t)(base[b[it]] + rank[it]);
+        const uint32_t slot = off[b[it]] + rank[it];
+        uint4 *dst = srec + 4 * slot;
         // bracket (-1, n) for a query without a k-mer bracket; an entry
         // record's bracket comes from its k-mer entry
         dst[0] = make_uint4(0xFFFFFFFFu, entry ? 0u : n, m, (uint32_t)q);
         dst[1] = make_uint4(r, entry ? kRecNeedsEntry : 0u, (uint32_t)qa, (uint32_t)(qa >> 32));
         dst[2] = make_uint4((uint32_t)w[0], (uint32_t)(w[0] >> 32), (uint32_t)w[1], (uint32_t)(w[1] >> 32));
         dst[3] = make_uint4((uint32_t)w[2], (uint32_t)(w[2] >> 32), (uint32_t)w[3], (uint32_t)(w[3] >> 32));
+        slot_bucket[slot] = b[it];
+    }
+    __syncthreads();
+    // copy the runs out, 16 bytes per thread per step
+    const uint32_t words = 4u * n_valid;
+    for (uint32_t c = threadIdx.x; c < words; c += kScatterThreads) {
+        const uint32_t slot = c >> 2;
+        const uint32_t bk = slot_bucket[slot];
+        const uint64_t g = (uint64_t)base[bk] + (slot - off[bk]);
+        list[4 * g + (c & 3u)] = srec[c];
     }
 }
 
@@ -193,10 +236,11 @@ cudaError_t launch_bucketed_worklist(const SearchLaunch &L, uint4 *wrec_in, cuda
     else
         bucket_count_kernel<false><<<(unsigned)tiles, kBucketThreads, 0, s>>>(L);
     bucket_scan_kernel<<<1, 32, 0, s>>>(L);
-    if (single)
-        bucket_scatter_kernel<true><<<(unsigned)tiles, kBucketThreads, 0, s>>>(L, wrec_in);
-    else
-        bucket_scatter_kernel<false><<<(unsigned)tiles, kBucketThreads, 0, s>>>(L, wrec_in);
+    const uint64_t stiles = (L.n_q + kScatterTile - 1) / kScatterTile;
+    auto scatter = single ? bucket_scatter_kernel<true> : bucket_scatter_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+    if (e != cudaSuccess) return e;
+    scatter<<<(unsigned)stiles, kScatterThreads, kScatterSmem, s>>>(L, wrec_in);
     return cudaGetLastError();
 }
 

@@ -122,23 +122,21 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
         } else {
             q = base + lane;
             qa = nqa - a.first;
-            uint64_t qe = nqe - a.first;
+            const uint64_t qe = nqe - a.first;
             r = nr;
             if (base + stride + lane < a.n_q) {
                 nqa = __ldg(a.q_off + base + stride + lane);
                 nqe = __ldg(a.q_off + base + stride + lane + 1);
                 if (!kSingle) nr = __ldg(a.q_ref + base + stride + lane);
             }
+            const bool rc = a.revcomp || (a.strand_bits && (r & kStrandBit));
+            if (a.strand_bits) r &= ~kStrandBit;
             const bool range_ok = live && qa <= qe && qe <= a.total && qe - qa < (1ull << 31);
             if (live && !range_ok) any_bad = true;
-            if (range_ok && a.revcomp) {  // the reverse complement sits at the mirrored range
-                const uint64_t t = a.total - qe;
-                qe = a.total - qa;
-                qa = t;
-            }
             ok = range_ok && r < a.n_refs;
             if (range_ok && r >= a.n_refs) any_bad_ref = true;
             m = ok ? (uint32_t)(qe - qa) : 0u;
+            if (range_ok) qa = strand_start(qa, qe, a.total, rc, a.rc_base);
 
             // First 128 bases and the validity of every base of the query.
             if (!load_query_head(tq, a.tv, ok ? (qa >> 5) : 0, (uint32_t)(qa & 31u), m, ok && m > 0, w)) {

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_gather_kernel(const __gr
         if (q >= a.n_q) continue;
         a.out_offsets[q] = off;
         if (pos == nullptr || k == 0) continue;
-        const uint32_t ref = a.q_ref ? a.q_ref[q] : 0u;
+        const uint32_t ref = a.q_ref ? (a.q_ref[q] & ~kStrandBit) : 0u;  // bit 31: the strand, not the reference
         const RefDesc &d = a.refs.r[ref < a.n_refs ? ref : 0];
         const uint64_t kk = (ref < a.n_refs && r.lo <= d.n && k <= d.n - r.lo) ? k : 0;  // never past SA
         const IdxT *sa = reinterpret_cast<const IdxT *>(d.sa);

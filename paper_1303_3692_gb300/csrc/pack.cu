@@ -140,12 +140,16 @@ cudaError_t launch_pack_batch(const SearchLaunch &L, uint64_t *tq, uint32_t *tv,
     const uint64_t cap = (uint64_t)device_sm_count() * 8;
     const unsigned blocks = (unsigned)(want < cap ? want : cap);
     const bool aligned = ((uintptr_t)L.ascii & 15u) == 0;
-    if (L.revcomp)
-        pack_batch_rc_kernel<<<blocks, threads, 0, s>>>(reinterpret_cast<const uint8_t *>(L.ascii), L.total,
-                                                        L.nwords, tq, tv);
-    else
-        pack_batch_kernel<<<blocks, threads, 0, s>>>(reinterpret_cast<const uint8_t *>(L.ascii), L.total, L.nwords,
-                                                     tq, tv, aligned);
+    const uint8_t *ascii = reinterpret_cast<const uint8_t *>(L.ascii);
+    // the forward packing, the reverse-complement one, or both (forward
+    // first, the other from word nwords + SA_TQ_PAD_WORDS on) when each query
+    // names its strand
+    if (!L.revcomp || L.strand_bits)
+        pack_batch_kernel<<<blocks, threads, 0, s>>>(ascii, L.total, L.nwords, tq, tv, aligned);
+    if (L.revcomp || L.strand_bits) {
+        const uint64_t half = L.strand_bits ? L.nwords + SA_TQ_PAD_WORDS : 0;
+        pack_batch_rc_kernel<<<blocks, threads, 0, s>>>(ascii, L.total, L.nwords, tq + half, tv + half);
+    }
     return cudaGetLastError();
 }
 

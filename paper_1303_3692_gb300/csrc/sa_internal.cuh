@@ -143,6 +143,18 @@ __device__ __forceinline__ uint64_t pack_word(const uint8_t *__restrict__ a, uin
     return word;
 }
 
+// q_ref bit 31 under SA_PARAM_STRAND_PER_QUERY: search the query's reverse complement.
+constexpr uint32_t kStrandBit = 0x80000000u;
+
+// A query's first base in the packed batch tq: its own range [qa, qe), or
+// for the other strand the mirrored range of the reverse-complement packing,
+// which starts at base rc_base of tq (base i of that packing is the
+// complement of batch base total - 1 - i).
+__device__ __forceinline__ uint64_t strand_start(uint64_t qa, uint64_t qe, uint64_t total, bool rc,
+                                                 uint64_t rc_base) {
+    return rc ? rc_base + (total - qe) : qa;
+}
+
 // Bits [lo, hi) of a 32-bit mask (0 <= lo <= hi <= 32).
 __device__ __forceinline__ uint32_t bit_range(uint32_t lo, uint32_t hi) {
     const uint32_t upto = hi >= 32u ? 0xFFFFFFFFu : ((1u << hi) - 1u);
@@ -383,6 +395,8 @@ struct SearchLaunch {
     uint32_t threads, blocks, chunk;
     uint32_t front_probes;    // probes per query in the first pass
     bool revcomp;             // search every query's reverse complement (the batch is packed reversed)
+    bool strand_bits;         // q_ref bit 31 selects each query's strand (both packings in tq)
+    uint64_t rc_base;         // first base of the reverse-complement packing in tq (0: it is the only one)
     bool expire_waits;        // test hook: the bounded key-table wait gives up at once
     uint32_t trunc_cap;       // the locate cap of sa_search_locate (SA_RESULT_TRUNCATED), else ~0u
     // k-mer order (bucket.cu)

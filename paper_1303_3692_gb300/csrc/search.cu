@@ -369,12 +369,14 @@ __global__ void __launch_bounds__(256) search_plain_kernel(const __grid_constant
     if (q >= a.n_q) return;
     uint64_t a0 = __ldg(a.q_off + q) - a.first;
     uint64_t a1 = __ldg(a.q_off + q + 1) - a.first;
-    const uint32_t r = a.q_ref ? __ldg(a.q_ref + q) : 0u;
+    uint32_t r = a.q_ref ? __ldg(a.q_ref + q) : 0u;
+    const bool rc = a.revcomp || (a.strand_bits && (r & kStrandBit));
+    if (a.strand_bits) r &= ~kStrandBit;
     const bool range_ok = a0 <= a1 && a1 <= a.total && a1 - a0 < (1ull << 31);
-    if (range_ok && a.revcomp) {  // the reverse complement sits at the mirrored range
-        const uint64_t t = a.total - a1;
-        a1 = a.total - a0;
-        a0 = t;
+    if (range_ok) {  // the other strand sits at the mirrored range of its packing
+        const uint64_t len = a1 - a0;
+        a0 = strand_start(a0, a1, a.total, rc, a.rc_base);
+        a1 = a0 + len;
     }
     bool bad = !range_ok;
     if (range_ok) {  // every base of the query must be one of A, C, G, T

@@ -40,6 +40,8 @@ SA_PARAM_REVERSE_COMPLEMENT = 0x2
 SA_PARAM_EXPIRE_WAITS = 0x4
 SA_PARAM_KMER_ORDER = 0x8
 SA_PARAM_INPUT_ORDER = 0x10
+SA_PARAM_STRAND_PER_QUERY = 0x20
+STRAND_BIT = 0x80000000  # q_ref bit 31 under SA_PARAM_STRAND_PER_QUERY
 SA_LOCATE_NOALLOC_MAX_QUERIES = 1 << 26
 SA_RESULT_INVALID = 0x1
 SA_RESULT_TRUNCATED = 0x2

@@ -35,6 +35,7 @@ class Request:
     offsets: np.ndarray   # int64, n + 1 offsets starting at 0
     arrival: float        # seconds since the start of the trace
     cap: int = 0          # positions to locate per query (0: counts only)
+    rc: bool = False      # search the queries' reverse complements (the other strand)
     results: Optional[np.ndarray] = None   # (n, 4) int64: lo, hi, count, flags
     pos_offsets: Optional[np.ndarray] = None  # (n + 1) int64 when cap > 0
     positions: Optional[np.ndarray] = None    # located positions, suffix-array order per query
@@ -50,13 +51,14 @@ class Request:
         return int(self.offsets[-1])
 
 
-def scratch_bytes(n_q: int, n_bases: int) -> int:
-    """Device scratch one search call takes from the library's pool: the
-    packed batch (8 bytes per 32 bases) and its validity masks (4 bytes per 32
-    bases), 64 bytes of worklist room per query, small flags, and 256 bytes of
-    alignment per allocation."""
-    words = (n_bases + 31) // 32 + 6
-    return 12 * words + 64 * n_q + 80 + 5 * 256
+def scratch_bytes(n_q: int, n_bases: int, both_strands: bool = False) -> int:
+    """Device scratch one search call takes from the library's pool, at most:
+    the packed batch (8 bytes per 32 bases) and its validity masks (4 bytes
+    per 32 bases), twice when queries name their strands; 64 bytes of worklist
+    room per query; in k-mer order another 64-byte record and a 2-byte bucket
+    per query; small flags, and 256 bytes of alignment per allocation."""
+    words = ((n_bases + 31) // 32 + 6) * (2 if both_strands else 1)
+    return 12 * words + 64 * n_q + 66 * n_q + 2 * 257 * 4 + 80 + 8 * 256
 
 
 def kept(counts: np.ndarray, cap: int) -> np.ndarray:
@@ -80,13 +82,17 @@ def form_batch(queue: List[Request], max_q: int, max_bases: int, budget: int):
     library scratch stay within max_q, max_bases and the device-memory budget;
     the first request that does not fit ends the batch (no reordering)."""
     nq = nb = 0
+    both = False
     i = 0
     while i < len(queue):
         r = queue[i]
-        if nq + r.n > max_q or nb + r.nbases > max_bases or scratch_bytes(nq + r.n, nb + r.nbases) > budget:
+        b2 = both or r.rc
+        if (nq + r.n > max_q or nb + r.nbases > max_bases
+                or scratch_bytes(nq + r.n, nb + r.nbases, both_strands=b2) > budget):
             break
         nq += r.n
         nb += r.nbases
+        both = b2
         i += 1
     return queue[:i], queue[i:]
 
@@ -159,11 +165,12 @@ class Server:
         nq = sum(r.n for r in reqs)
         nb = sum(r.nbases for r in reqs)
         ho = slot.h_offsets.numpy()
-        hr = slot.h_qref.numpy()
+        hr = slot.h_qref.numpy().view(np.uint32)
+        both = any(r.rc for r in reqs)
         q, b = 0, 0
         for r in reqs:
             ho[q:q + r.n + 1] = r.offsets + b
-            hr[q:q + r.n] = r.ref
+            hr[q:q + r.n] = r.ref | (sa.STRAND_BIT if r.rc else 0)
             q += r.n
             b += r.nbases
         with torch.cuda.stream(slot.stream):
@@ -176,6 +183,8 @@ class Server:
             slot.qref[:nq].copy_(slot.h_qref[:nq], non_blocking=True)
             p = sa.sa_search_params() if self.params is None else sa.sa_search_params.from_buffer_copy(self.params)
             p.flags |= sa.SA_PARAM_Q_RANGE
+            if both:  # some requests want the other strand: bit 31 of their reference ids
+                p.flags |= sa.SA_PARAM_STRAND_PER_QUERY
             p.q_first, p.q_total = 0, nb
             slot.cap = max((r.cap for r in reqs), default=0)
             if nq and slot.cap:  # search and locate in one call, up to the batch's largest cap
@@ -242,9 +251,12 @@ class Server:
     def idle(self) -> bool:
         return not self.queue and all(s.event is None for s in self.slots)
 
-    def run(self, trace: Sequence[Request], clock: Callable[[], float] = time.perf_counter) -> dict:
+    def run(self, trace: Sequence[Request], clock: Callable[[], float] = time.perf_counter,
+            poll_s: float = 50e-6) -> dict:
         """Replays the trace in real time (arrival times relative to the start;
-        a trace whose arrivals are all 0 measures the saturated throughput)."""
+        a trace whose arrivals are all 0 measures the saturated throughput).
+        Between events the loop sleeps: until the next arrival when nothing is
+        in flight, else for poll_s before it looks at the batches again."""
         pending = sorted(trace, key=lambda r: r.arrival)
         i = 0
         t0 = clock()
@@ -254,6 +266,13 @@ class Server:
                 self.submit(pending[i])
                 i += 1
             self.pump(now)
+            nxt = pending[i].arrival - (clock() - t0) if i < len(pending) else math.inf
+            busy = any(s.event is not None for s in self.slots)
+            wait = min(nxt, poll_s) if busy else nxt
+            if self.queue and not busy:
+                wait = 0.0  # a free slot and a waiting request: no reason to sleep
+            if 0 < wait < math.inf:
+                time.sleep(wait)
         return summarize(trace, self.batches)
 
 
@@ -274,24 +293,40 @@ def summarize(trace: Sequence[Request], batches: int) -> dict:
 
 
 def run_plain(refs: Sequence["sa.Index"], trace: Sequence[Request],
-              clock: Callable[[], float] = time.perf_counter) -> dict:
+              clock: Callable[[], float] = time.perf_counter, kernel: str = "optimized") -> dict:
     """One search call per request, in arrival order, each on the default stream
-    and waited for before the next (no coalescing, no overlap)."""
+    and waited for before the next (no coalescing, no overlap).  kernel
+    "optimized" makes each call with the library's search (and locate) in one
+    call; "plain" with the one-thread-per-query rendering of Alg. 1
+    (sa_search_batch_plain), then sa_locate for a request that wants
+    positions."""
     import torch
 
+    if kernel not in ("optimized", "plain"):
+        raise ValueError("kernel must be 'optimized' or 'plain'")
     dev = torch.device("cuda", torch.cuda.current_device())
     pending = sorted(trace, key=lambda r: r.arrival)
     t0 = clock()
     for r in pending:
-        while clock() - t0 < r.arrival:
-            pass
+        wait = r.arrival - (clock() - t0)
+        if wait > 0:
+            time.sleep(wait)
         bases = r.bases[:r.nbases].to(dev, non_blocking=True) if r.nbases else torch.zeros(1, dtype=torch.uint8,
                                                                                              device=dev)
         offs = torch.from_numpy(r.offsets).to(dev, non_blocking=True)
         p = sa.sa_search_params()
-        p.flags = sa.SA_PARAM_Q_RANGE
+        p.flags = sa.SA_PARAM_Q_RANGE | (sa.SA_PARAM_REVERSE_COMPLEMENT if r.rc else 0)
         p.q_first, p.q_total = 0, r.nbases
-        if r.cap:
+        if kernel == "plain" and r.rc:
+            raise ValueError("the plain kernel searches the forward strand only")
+        if kernel == "plain":
+            res = sa.sa_search_batch_plain(refs[r.ref], bases, offs)
+            if r.cap:
+                lo_offs, pos = sa.sa_locate(refs[r.ref], res, r.cap)
+                r.pos_offsets = lo_offs.cpu().numpy()
+                r.positions = pos[:int(r.pos_offsets[-1])].cpu().numpy()
+                res[:, 3] = torch.where(res[:, 2] > r.cap, sa.SA_RESULT_TRUNCATED, res[:, 3])
+        elif r.cap:
             res, lo_offs, pos = sa.sa_search_locate(refs[r.ref], bases, offs, r.cap, params=p)
             r.pos_offsets = lo_offs.cpu().numpy()
             r.positions = pos[:int(r.pos_offsets[-1])].cpu().numpy()
@@ -304,12 +339,13 @@ def run_plain(refs: Sequence["sa.Index"], trace: Sequence[Request],
 
 
 def make_trace(ref_pools, rate: float, duration: float, seed: int, q_range=(1, 100_000),
-               caps: Sequence[int] = (0,)) -> List[Request]:
+               caps: Sequence[int] = (0,), rc_frac: float = 0.0) -> List[Request]:
     """Poisson arrivals (mean `rate` per second over `duration` seconds); each
     request targets a uniformly drawn reference, holds a log-uniform number of
     queries in q_range, sliced from that reference's pool of pinned queries
     (ref_pools[r] = (pinned bases tensor, offsets int64 numpy)), and asks for a
-    locate cap drawn uniformly from caps (0: counts only)."""
+    locate cap drawn uniformly from caps (0: counts only); a fraction rc_frac
+    of the requests ask for the other strand.""" 
     rng = np.random.default_rng(seed)
     t, reqs = 0.0, []
     while True:
@@ -324,5 +360,6 @@ def make_trace(ref_pools, rate: float, duration: float, seed: int, q_range=(1, 1
         s = int(rng.integers(0, pool_n - n + 1))
         o = offs[s:s + n + 1] - offs[s]
         cap = int(caps[int(rng.integers(0, len(caps)))]) if len(caps) > 1 else int(caps[0])
-        reqs.append(Request(len(reqs), r, bases[int(offs[s]):int(offs[s + n])], o, t, cap=cap))
+        rc = bool(rng.random() < rc_frac) if rc_frac > 0 else False
+        reqs.append(Request(len(reqs), r, bases[int(offs[s]):int(offs[s + n])], o, t, cap=cap, rc=rc))
     return reqs

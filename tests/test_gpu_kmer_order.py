@@ -130,3 +130,58 @@ def test_kmer_order_search_locate(sa):
     assert np.array_equal(res[:, 0], lo) and np.array_equal(res[:, 1], hi)
     for q in range(0, qo.size - 1, 7):
         assert np.array_equal(pos[offs[q]:offs[q + 1]].astype(np.int64), oracle.locate(osa, lo[q], hi[q], 8))
+
+
+@pytest.mark.parametrize("order", ["kmer", "input"])
+def test_strand_per_query(sa, order):
+    """SA_PARAM_STRAND_PER_QUERY: bit 31 of a query's reference id asks for its
+    reverse complement; the others in the same batch search the forward
+    strand (two references, both search orders, and the plain kernel)."""
+    refs = [datagen.reference(n, 95 + n, sd_cover=0.1, tandem_cover=0.05) for n in (60_000, 35_000)]
+    idxs = [sa.sa_build(torch.from_numpy(r).cuda()) for r in refs]
+    rng = np.random.default_rng(96)
+    n_q = 6000
+    q_ref = rng.integers(0, 2, n_q).astype(np.uint32)
+    rc = rng.random(n_q) < 0.5
+    # each reference's queries, interleaved in the batch by q_ref
+    per = [datagen.queries(refs[i], int((q_ref == i).sum()), 97 + i, m=(5, 180), frac_sampled=0.8, subs=(0, 1))
+           for i in range(2)]
+    nxt = [0, 0]
+    parts, lens = [], []
+    for q in range(n_q):
+        i = q_ref[q]
+        b_, o_, _ = per[i]
+        j = nxt[i]
+        nxt[i] += 1
+        parts.append(b_[o_[j]:o_[j + 1]])
+        lens.append(o_[j + 1] - o_[j])
+    qb = np.concatenate(parts)
+    qo = np.zeros(n_q + 1, dtype=np.int64)
+    np.cumsum(lens, out=qo[1:])
+    flagged = q_ref | np.where(rc, sa.STRAND_BIT, 0).astype(np.uint32)
+    fl = sa.SA_PARAM_STRAND_PER_QUERY | (sa.SA_PARAM_KMER_ORDER if order == "kmer" else sa.SA_PARAM_INPUT_ORDER)
+    got = sa.sa_search_batch(idxs, torch.from_numpy(qb).cuda(), torch.from_numpy(qo).cuda(),
+                             q_ref=torch.from_numpy(flagged).cuda(), params=sa.sa_search_params(flags=fl)).cpu().numpy()
+    comp = np.zeros(256, dtype=np.uint8)
+    for a_, b_ in zip(b"ACGT", b"TGCA"):
+        comp[a_] = b_
+    Ts = [oracle.normalize(r) for r in refs]
+    sas = [oracle.sa_naive(T) for T in Ts]
+    for q in range(n_q):
+        P = qb[qo[q]:qo[q + 1]]
+        if rc[q]:
+            P = comp[P][::-1]
+        lo, hi = oracle.search(Ts[q_ref[q]], sas[q_ref[q]], P)
+        assert got[q, :3].tolist() == [lo, hi, hi - lo], q
+    if order == "input":
+        # a call without the flag (the plain kernel takes no params) reads bit
+        # 31 as part of the id: out of range, so those queries are invalid
+        plain = sa.sa_search_batch_plain(idxs, torch.from_numpy(qb).cuda(), torch.from_numpy(qo).cuda(),
+                                         q_ref=torch.from_numpy(flagged).cuda())
+        assert (plain.cpu().numpy()[rc, 3] == sa.SA_RESULT_INVALID).all()
+    # locate ignores the strand bit
+    offs, pos = sa.sa_locate(idxs, torch.from_numpy(got).cuda(), 4, q_ref=torch.from_numpy(flagged).cuda())
+    offs, pos = offs.cpu().numpy(), pos.cpu().numpy()
+    for q in range(0, n_q, 13):
+        want = oracle.locate(sas[q_ref[q]], int(got[q, 0]), int(got[q, 1]), 4)
+        assert np.array_equal(pos[offs[q]:offs[q + 1]].astype(np.int64), want)

@@ -268,7 +268,7 @@ def test_errors(sa):
         sa.sa_search_batch([idx, idx64], _dev(qb), _dev(qo), q_ref=_dev(np.array([0, 1], dtype=np.uint32)))
     # empty batch
     empty = sa.sa_search_batch(idx, _dev(qb), _dev(np.zeros(1, dtype=np.int64)))
-    assert empty.shape == (0, 3)
+    assert empty.shape == (0, sa.RESULT_FIELDS)
 
 
 def test_save_load_roundtrip(sa, tmp_path):
@@ -352,7 +352,7 @@ def test_q_range_param_sub_batch(sa):
     assert np.array_equal(a[:, 0].numpy(), lo) and np.array_equal(a[:, 1].numpy(), hi)
     p.q_total = int(sub[-1] - sub[0]) - 5
     c = sa.sa_search_batch(idx, qb_d, sub_d, params=p).cpu()
-    assert (c[-1] == -1).all() and torch.equal(c[:-1], a[:-1])
+    assert (c[-1][:3] == -1).all() and c[-1][3] == sa.SA_RESULT_INVALID and torch.equal(c[:-1], a[:-1])
 
 
 def _check_positions(res, offs, pos, lo, hi, osa, cap):
