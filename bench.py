@@ -513,7 +513,7 @@ def run_human_sized(args, world, rank, local):
     at_index = min(idx_est, free_b - (8 << 30)) & ~((1 << 30) - 1)
     ceiling = {}
     for size in sorted({64 << 30, at_index}):
-        if size <= 0 or size > free_b - (4 << 30):
+        if args.no_rr_probe or size <= 0 or size > free_b - (4 << 30):
             continue
         for rb in (32, 64):
             ceiling[f"{size >> 30}GB_{rb}B"] = sa.sa_random_read_rate(size, 1024, 64, read_bytes=rb) / 1e9
@@ -544,7 +544,8 @@ def run_human_sized(args, world, rank, local):
         p, tune = autotune.autotune(idx, qb_d, qo_d, sample=2_000_000, use_cache=False)
     else:
         p = sa.sa_search_params(front_probes=args.front_probes)
-    p.flags = sa.SA_PARAM_Q_RANGE
+    p.flags = sa.SA_PARAM_Q_RANGE | {"auto": 0, "kmer": sa.SA_PARAM_KMER_ORDER,
+                                     "input": sa.SA_PARAM_INPUT_ORDER}[args.order]
     p.q_first, p.q_total = 0, m_total
     sa.sa_search_batch(idx, qb_d, qo_d, out=res, params=p)
     o, _ = sa.sa_locate(idx, res, cap, out_pos=torch.empty(1, dtype=torch.int64, device=dev), capacity=0)
@@ -619,14 +620,15 @@ def run_human_sized(args, world, rank, local):
     h2d = int(qb_h.numel() + qo_h.numel() * 8)
     d2h = int(res_h.numel() * 8 + offs_h.numel() * 8 + total_pos * 8)
     # the plain pinned copy rate of this link, for context
-    probe_d = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
+    probe_n = min(1 << 30, qb_h.numel())
+    probe_d = torch.empty(probe_n, dtype=torch.uint8, device=dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     for _ in range(4):
-        probe_d.copy_(qb_h[:1 << 30], non_blocking=True)
+        probe_d.copy_(qb_h[:probe_n], non_blocking=True)
     b.record(stream)
     torch.cuda.synchronize()
-    h2d_gbs = 4 * (1 << 30) / (a.elapsed_time(b) / 1e3) / 1e9
+    h2d_gbs = 4 * probe_n / (a.elapsed_time(b) / 1e3) / 1e9
     del probe_d
     qb_d = torch.from_numpy(w.q_bases).to(dev)
 
@@ -1169,6 +1171,9 @@ def main():
                                            "serving", "paper-shaped"],
                     default="human-sized")
     ap.add_argument("--autotune", action="store_true", help="tune the launch shape before timing (human-sized)")
+    ap.add_argument("--order", choices=["auto", "kmer", "input"], default="auto",
+                    help="search order of the human-sized line (auto: the library's choice)")
+    ap.add_argument("--no-rr-probe", action="store_true", help="skip the random-read ceiling probes")
     ap.add_argument("--human-queries", type=int, default=110_000_000,
                     help="queries per step of the 3.1 Gbp workload (100M sampled + 10M random)")
     ap.add_argument("--serve-seconds", type=float, default=2.0)

@@ -63,6 +63,10 @@ extern "C" {
  * (sa_suffix_array_host) and upload it, instead of prefix doubling on the
  * GPU; the rest of the index is built on the GPU either way */
 #define SA_BUILD_HOST 0x8u
+/* build the suffix array on the GPU by the DC3 construction of Section III
+ * (the steps of sa_suffix_array_host, as data-parallel passes) instead of
+ * prefix doubling; the same array either way */
+#define SA_BUILD_DC3 0x10u
 /* k of the k-mer table, 1..15, in bits 8-11; 0 there picks k automatically. */
 #define SA_KMER_K(k) ((uint32_t)(k) << 8)
 
@@ -193,7 +197,8 @@ typedef struct sa_search_params {
  *  text   n bytes of bases, host or device memory.
  *  n      number of bases, 1 <= n < 2^32 - 1.
  *  flags  SA_W32 or SA_W64 (exactly one): element width of the suffix array;
- *         optionally SA_NO_KMER or SA_KMER_K(k), and SA_BUILD_HOST.
+ *         optionally SA_NO_KMER or SA_KMER_K(k), and SA_BUILD_HOST or
+ *         SA_BUILD_DC3 (not both).
  *  stream CUDA stream (cudaStream_t) or NULL.
  *  out    receives the new index.
  *
@@ -425,6 +430,55 @@ int sa_copy_suffix_array(const sa_index *idx, void *dst, void *stream);
  * and 4 n more for width 8).
  */
 int sa_suffix_array_host(const char *text, uint64_t n, uint32_t width, void *sa);
+
+/*
+ * sa_suffix_array_gpu -- the suffix array of a text, built on the GPU into a
+ * caller-owned device buffer (no index): by prefix doubling, or with
+ * SA_BUILD_DC3 in flags by the DC3 construction of Section III.
+ *
+ *  text   n bases (A, C, G, T, either case), host or device memory.
+ *  n      1 <= n < 2^32 - 1.
+ *  width  4 or 8: element width of sa.
+ *  flags  0 or SA_BUILD_DC3.
+ *  sa     device buffer of n elements (Table I order).
+ *  stream CUDA stream or NULL.  Synchronous.
+ *
+ * Scratch comes from the library's pool: about 12 n bytes (prefix doubling
+ * 46 n) besides sa.  Errors: SA_ERR_ARG, SA_ERR_BASE, SA_ERR_NOMEM, SA_ERR_CUDA.
+ */
+int sa_suffix_array_gpu(const char *text, uint64_t n, uint32_t width, uint32_t flags, void *sa, void *stream);
+
+/*
+ * The suffix tree (Section III), flattened for the GPU: the paper's
+ * comparison index (Table V times a suffix-tree search beside the
+ * suffix-array one).  Built from an index's suffix array and an LCP array
+ * (computed on the GPU) by the bottom-up traversal of LCP intervals on the
+ * host; one 32-byte record per internal node {first rank, last rank, string
+ * depth, a text position of its label, a child per base}, leaves being single
+ * ranks.  About 32 bytes of device memory per base.  For contrast: the
+ * suffix-array search is the product path.
+ */
+typedef struct sa_stree sa_stree;
+
+/* Builds the tree of idx's text.  Synchronous; the tree refers to idx, which
+ * must outlive it.  Host memory about 45 n bytes during the build.  Errors:
+ * SA_ERR_ARG, SA_ERR_NOMEM, SA_ERR_CUDA. */
+int sa_stree_build(const sa_index *idx, void *stream, sa_stree **out);
+
+/* The interval of every query by descending the tree, one GPU thread per
+ * query: the same results as sa_search_batch (Section IV's interval; misses at
+ * their insertion point; an invalid query all-ones with SA_RESULT_INVALID).
+ * q_bases, q_offsets (n_q + 1) and out (32-byte aligned) in device memory.
+ * Reads q_offsets[0] and q_offsets[n_q] back (one small synchronous copy).
+ * Errors: SA_ERR_ARG, SA_ERR_NOMEM, SA_ERR_CUDA. */
+int sa_stree_search(const sa_stree *t, const char *q_bases, const uint64_t *q_offsets, uint64_t n_q, sa_result *out,
+                    void *stream);
+
+/* Internal nodes and device bytes of a tree; either pointer may be NULL. */
+int sa_stree_info(const sa_stree *t, uint64_t *nodes, uint64_t *device_bytes);
+
+/* Releases the tree (synchronizes the device first); not its index. */
+void sa_stree_free(sa_stree *t);
 
 /* Releases the index and its device memory (synchronizes the device first). */
 void sa_free(sa_index *idx);

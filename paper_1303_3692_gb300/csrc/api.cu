@@ -525,7 +525,8 @@ int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_inde
     if (!text || n == 0 || n >= 0xFFFFFFFFull) return SA_ERR_ARG;
     const uint32_t wflags = flags & (SA_W32 | SA_W64);
     if (wflags != SA_W32 && wflags != SA_W64) return SA_ERR_ARG;
-    if (flags & ~(SA_W32 | SA_W64 | SA_NO_KMER | SA_BUILD_HOST | SA_KMER_K(15))) return SA_ERR_ARG;
+    if (flags & ~(SA_W32 | SA_W64 | SA_NO_KMER | SA_BUILD_HOST | SA_BUILD_DC3 | SA_KMER_K(15))) return SA_ERR_ARG;
+    if ((flags & SA_BUILD_HOST) && (flags & SA_BUILD_DC3)) return SA_ERR_ARG;
     const uint32_t want_k = (flags >> 8) & 15u;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     sa_index *idx = new (std::nothrow) sa_index();
@@ -586,6 +587,8 @@ int sa_build(const char *text, uint64_t n, uint32_t flags, void *stream, sa_inde
             host_text = copy.data();
         }
         st = build_suffix_array_host(idx, host_text, stream);
+    } else if (flags & SA_BUILD_DC3) {
+        st = build_suffix_array_dc3(idx, s);
     } else {
         st = build_suffix_array(idx, s);
     }
@@ -1099,6 +1102,41 @@ void sa_free(sa_index *idx) {
     if (!idx) return;
     cudaDeviceSynchronize();
     free_index(idx);
+}
+
+int sa_suffix_array_gpu(const char *text, uint64_t n, uint32_t width, uint32_t flags, void *sa_out, void *stream) {
+    NvtxRange range("sa_suffix_array_gpu");
+    if (!text || !sa_out || n == 0 || n >= 0xFFFFFFFFull || (width != 4 && width != 8) || (flags & ~SA_BUILD_DC3))
+        return SA_ERR_ARG;
+    if (!on_device(sa_out)) return SA_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    sa_index tmp;  // a text and a suffix array only: what the builders read and write
+    memset(&tmp, 0, sizeof tmp);
+    tmp.n = n;
+    tmp.width = width;
+    tmp.nwords = (n + 31) / 32;
+    tmp.sa = sa_out;
+    if (cudaGetDevice(&tmp.device) != cudaSuccess) return SA_ERR_CUDA;
+    int st = SA_OK;
+    {
+        Scratch sc{s};
+        cudaError_t err = cudaSuccess;
+        const char *text_d = device_view(text, n, sc, &err);
+        tmp.text = sc.get<uint64_t>(tmp.nwords + SA_PAD_WORDS);
+        int *flag = sc.get<int>(1);
+        if (sc.failed) return SA_ERR_NOMEM;
+        int hflag = 0;
+        if (err == cudaSuccess) err = cudaMemsetAsync(flag, 0, sizeof(int), s);
+        if (err == cudaSuccess) err = launch_pack_text(text_d, n, tmp.text, tmp.nwords + SA_PAD_WORDS, flag, s);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+        if (err != cudaSuccess) return status_from_cuda(err);
+        if (hflag) return SA_ERR_BASE;
+        st = (flags & SA_BUILD_DC3) ? build_suffix_array_dc3(&tmp, s) : build_suffix_array(&tmp, s);
+        cudaStreamSynchronize(s);
+    }
+    cudaMemPoolTrimTo(scratch_pool(tmp.device), 0);
+    return st;
 }
 
 int sa_search_order(const sa_index *const *refs, uint32_t n_refs, uint64_t n_q, const sa_search_params *params,

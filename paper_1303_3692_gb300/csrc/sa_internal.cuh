@@ -358,6 +358,8 @@ int device_sm_count();
 cudaError_t launch_pack_text(const char *ascii, uint64_t n, uint64_t *words, uint64_t nwords_padded,
                              int *err_flag, cudaStream_t s);
 int build_suffix_array(sa_index *idx, cudaStream_t s);
+// The same array by the paper's DC3 construction, on the GPU (dc3_gpu.cu).
+int build_suffix_array_dc3(sa_index *idx, cudaStream_t s);
 cudaError_t launch_build_keys(sa_index *idx, cudaStream_t s);
 cudaError_t launch_build_records(sa_index *idx, cudaStream_t s);
 cudaError_t launch_build_kmer(sa_index *idx, cudaStream_t s);

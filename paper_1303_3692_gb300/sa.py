@@ -35,6 +35,7 @@ SA_W32 = 0x1
 SA_W64 = 0x2
 SA_NO_KMER = 0x4
 SA_BUILD_HOST = 0x8
+SA_BUILD_DC3 = 0x10
 SA_PARAM_Q_RANGE = 0x1
 SA_PARAM_REVERSE_COMPLEMENT = 0x2
 SA_PARAM_EXPIRE_WAITS = 0x4
@@ -92,6 +93,11 @@ SIGNATURES = {
     "sa_random_read_rate": (ctypes.c_int, [_u64, _u32, _u32, ctypes.POINTER(ctypes.c_double), _vp]),
     "sa_random_read_rate_ex": (ctypes.c_int, [_u64, _u32, _u32, _u32, ctypes.POINTER(ctypes.c_double), _vp]),
     "sa_suffix_array_host": (ctypes.c_int, [_vp, _u64, _u32, _vp]),
+    "sa_suffix_array_gpu": (ctypes.c_int, [_vp, _u64, _u32, _u32, _vp, _vp]),
+    "sa_stree_build": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp)]),
+    "sa_stree_search": (ctypes.c_int, [_vp, _vp, _vp, _u64, _vp, _vp]),
+    "sa_stree_info": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
+    "sa_stree_free": (None, [_vp]),
     "sa_search_order": (ctypes.c_int, [ctypes.POINTER(_vp), _u32, _u64, ctypes.POINTER(sa_search_params),
                                        ctypes.POINTER(ctypes.c_int)]),
     "sa_scratch_info": (ctypes.c_int, [ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64),
@@ -202,15 +208,19 @@ class Index:
         sa_save(self, path)
 
 
-def sa_build(text, width: int = 32, stream=None, kmer_k: Optional[int] = None, host_build: bool = False) -> Index:
+def sa_build(text, width: int = 32, stream=None, kmer_k: Optional[int] = None, host_build: bool = False,
+             dc3: bool = False) -> Index:
     """Index one reference (ASCII bases, host or device).  kmer_k: None picks k
     automatically, 0 builds no k-mer table, 1..15 sets k.  host_build: build
-    the suffix array on the host by DC3 instead of on the GPU."""
+    the suffix array on the host by DC3 instead of on the GPU; dc3: build it on
+    the GPU by DC3 instead of prefix doubling."""
     flags = SA_W32 if width == 32 else SA_W64 if width == 64 else None
     if flags is None:
         raise ValueError("width must be 32 or 64")
     if host_build:
         flags |= SA_BUILD_HOST
+    if dc3:
+        flags |= SA_BUILD_DC3
     if kmer_k == 0:
         flags |= SA_NO_KMER
     elif kmer_k is not None:
@@ -396,3 +406,49 @@ def sa_search_order(refs, n_q: int, params=None) -> str:
     _check(lib().sa_search_order(arr, nr, n_q, None if params is None else ctypes.byref(params), ctypes.byref(v)),
            "sa_search_order")
     return "kmer" if v.value else "input"
+
+
+def sa_suffix_array_gpu(text, width: int = 32, dc3: bool = False, stream=None):
+    """The suffix array of text (ASCII bases, host or device) built on the GPU,
+    by prefix doubling or (dc3=True) by DC3; an int32/int64 CUDA tensor."""
+    n = int(text.numel() if torch is not None and isinstance(text, torch.Tensor) else len(text))
+    if width not in (32, 64):
+        raise ValueError("width must be 32 or 64")
+    out = torch.empty(max(n, 1), dtype=torch.int32 if width == 32 else torch.int64, device="cuda")
+    _check(lib().sa_suffix_array_gpu(_ptr(text), n, width // 8, SA_BUILD_DC3 if dc3 else 0, _ptr(out),
+                                     _stream(stream)), "sa_suffix_array_gpu")
+    return out[:n]
+
+
+class SuffixTree:
+    """The flattened suffix tree of an index's text (the paper's comparison
+    index); keeps the index alive while it exists."""
+
+    def __init__(self, idx: Index, stream=None):
+        h = _vp()
+        _check(lib().sa_stree_build(idx.handle, _stream(stream), ctypes.byref(h)), "sa_stree_build")
+        self._h, self.index = h, idx
+        nodes, b = _u64(), _u64()
+        _check(lib().sa_stree_info(self._h, ctypes.byref(nodes), ctypes.byref(b)), "sa_stree_info")
+        self.nodes, self.device_bytes = nodes.value, b.value
+
+    def search(self, q_bases, q_offsets, out=None, stream=None):
+        """[lo, hi, count, flags] per query (device tensors in and out)."""
+        n_q = int(q_offsets.numel() - 1)
+        if out is None:
+            out = _out_like(n_q, q_offsets)
+        _check_results_buffer(out, n_q, "sa_stree_search")
+        _check(lib().sa_stree_search(self._h, _ptr(q_bases), _ptr(q_offsets), n_q, _ptr(out), _stream(stream)),
+               "sa_stree_search")
+        return out
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and self._h.value and _lib is not None:
+            _lib.sa_stree_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
