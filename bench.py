@@ -70,7 +70,7 @@ TRAFFIC = {"kernel_sha": "b52eb447dc121722", "kernel": "search",
 # Sources of each phase's kernels (the traffic figure is tied to them).
 PHASE_SOURCES = {
     "pack_batch_kernel": ("pack.cu", "sa_internal.cuh"),
-    "search": ("front.cu", "search.cu", "sa_internal.cuh"),
+    "search": ("bucket.cu", "front.cu", "search.cu", "sa_internal.cuh"),
     "locate": ("locate.cu", "sa_internal.cuh"),
 }
 
@@ -264,6 +264,13 @@ PAPER_TABLE5_SA = {
     131072: (0.0398, 0.0505), 262144: (0.0579, 0.0789), 524288: (0.095, 0.13284), 1048576: (0.2716, 0.3214),
     2097152: (0.4762, 0.5545),
 }
+# Table V's suffix-tree columns: queries -> (STK, STT) in seconds on the GTX680.
+PAPER_TABLE5_ST = {
+    512: (0.0002, 0.0882), 1024: (0.0004, 0.0894), 2048: (0.0005, 0.0895), 4096: (0.0007, 0.0897),
+    8192: (0.0009, 0.091), 16384: (0.0021, 0.0922), 32768: (0.0063, 0.0965), 65536: (0.0081, 0.0985),
+    131072: (0.018, 0.1087), 262144: (0.044, 0.1449), 524288: (0.1781, 0.3135), 1048576: (0.22, 0.523),
+    2097152: (0.33, 0.929),
+}
 
 
 def run_paper_shaped(args, world, rank, local):
@@ -271,8 +278,10 @@ def run_paper_shaped(args, world, rank, local):
     batches of 2^9 .. 2^21, count only.  Per batch: the device step (pack +
     search, inputs resident, L2 flushed before each step) and the end-to-end
     call on pinned host queries with the results read back, beside the paper's
-    kernel (SAK) and total (SAT) times.  The line's value is the largest
-    batch's device rate."""
+    kernel (SAK) and total (SAT) times.  Beside it the flattened suffix tree of
+    the same text (Table V's comparison index) searches the same batches, its
+    results checked equal to the suffix array's.  The line's value is the
+    largest batch's device rate."""
     import torch
 
     import paper_1303_3692_gb300.sa as sa
@@ -287,12 +296,16 @@ def run_paper_shaped(args, world, rank, local):
     idx = sa.sa_build(torch.from_numpy(w.ref).to(dev))
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    tree = sa.SuffixTree(idx)
+    st_build_s = time.perf_counter() - t0
     m = 1024
     n_max = w.q_offsets.size - 1
     qb_d, qo_d = torch.from_numpy(w.q_bases).to(dev), torch.from_numpy(w.q_offsets).to(dev)
     qb_h, qo_h = torch.from_numpy(w.q_bases).pin_memory(), torch.from_numpy(w.q_offsets).pin_memory()
     out_d = torch.empty((n_max, sa.RESULT_FIELDS), dtype=torch.int64, device=dev)
     out_h = torch.empty((n_max, sa.RESULT_FIELDS), dtype=torch.int64).pin_memory()
+    st_out = torch.empty((n_max, sa.RESULT_FIELDS), dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     sizes = sorted({q for q in PAPER_TABLE5_SA if q <= n_max} | {n_max})
@@ -330,9 +343,27 @@ def run_paper_shaped(args, world, rank, local):
                 t1 = time.perf_counter()
                 e2e()
                 e2e_ms.append((time.perf_counter() - t1) * 1e3)
+            # the suffix tree on the same batch (its call reads two offsets back first)
+            st_q = st_out[:q]
+            for _ in range(args.warmup):
+                tree.search(qb_d, qo_q, out=st_q)
+            torch.cuda.synchronize()
+            st_ms = []
+            for _ in range(args.steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                tree.search(qb_d, qo_q, out=st_q)
+                b.record(stream)
+                torch.cuda.synchronize()
+                st_ms.append(a.elapsed_time(b))
+            st_equal = bool(torch.equal(st_q, out_q))
             sak, sat = PAPER_TABLE5_SA.get(q, (None, None))
+            stk, stt = PAPER_TABLE5_ST.get(q, (None, None))
             sweep.append({"queries": q, "device_ms": dev_ms, "device_queries_per_s": q / dev_ms * 1e3,
-                          "e2e_ms": statistics.median(e2e_ms), "paper_sak_s": sak, "paper_sat_s": sat})
+                          "e2e_ms": statistics.median(e2e_ms), "paper_sak_s": sak, "paper_sat_s": sat,
+                          "st_device_ms": statistics.median(st_ms), "st_over_sa": statistics.median(st_ms) / dev_ms,
+                          "st_equals_sa": st_equal, "paper_stk_s": stk, "paper_stt_s": stt})
     if rank != 0:
         return
     top = sweep[-1]
@@ -350,10 +381,75 @@ def run_paper_shaped(args, world, rank, local):
                 "h2d_bytes_per_step": int(w.q_offsets[n_max]) + (n_max + 1) * 8,
                 "d2h_bytes_per_step": n_max * 32, "ms_per_step": top["e2e_ms"]},
         "sweep": sweep, "build_s": build_s, "datagen_s": gen_s, "gpu_launches": args.steps * 3,
+        "suffix_tree": {"nodes": tree.nodes, "node_bytes": tree.device_bytes,
+                        "suffix_array_bytes": int(w.ref.size) * 4, "build_s": st_build_s,
+                        "all_batches_equal_sa": all(r["st_equals_sa"] for r in sweep),
+                        "note": "the tree's descent also reads the text and, at leaves, the suffix array"},
         "clocks": clk.summary(),
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args)
+    print(json.dumps(line), flush=True)
+
+
+def run_build(args, world, rank, local):
+    """Suffix-array construction on the GPU by Section III's method (DC3) and by
+    prefix doubling (the library's default builder), on the human-like text at
+    10^8 bases (int32 array) and 3.1 * 10^9 bases (int64): wall time of each
+    synchronous call with the text resident, the two arrays checked equal.
+    The line's value is DC3's rate at the larger size."""
+    import torch
+
+    import paper_1303_3692_gb300.sa as sa
+    from paper_1303_3692_gb300 import datagen
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    warm = torch.from_numpy(datagen.reference(100_000, 7)).to(dev)
+    for dc3 in (False, True):  # module load and memory pool, untimed
+        sa.sa_suffix_array_gpu(warm, 32, dc3=dc3)
+    torch.cuda.synchronize()
+    rows = []
+    steps = max(1, min(args.steps, 3))
+    with Clocks(local) as clk:
+        for n_full, width in ((100_000_000, 32), (3_100_000_000, 64)):
+            n = max(20_000, int(n_full * args.scale))
+            t0 = time.perf_counter()
+            ref = datagen.reference(n, datagen.SEED0 + 4, gc=0.41, family_cover=0.45, tandem_cover=0.03)
+            gen_s = time.perf_counter() - t0
+            d = torch.from_numpy(ref).to(dev)
+            del ref
+            row = {"n": n, "width_bits": width, "datagen_s": gen_s}
+            arrays = {}
+            for name, dc3 in (("prefix_doubling", False), ("dc3", True)):
+                ts = []
+                for _ in range(steps):
+                    arrays.pop(name, None)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    arrays[name] = sa.sa_suffix_array_gpu(d, width, dc3=dc3)
+                    torch.cuda.synchronize()
+                    ts.append(time.perf_counter() - t0)
+                row[name + "_s"] = statistics.median(ts)
+                row[name + "_bases_per_s"] = n / row[name + "_s"]
+            row["equal"] = bool(torch.equal(arrays["prefix_doubling"], arrays["dc3"]))
+            row["dc3_over_doubling"] = row["dc3_s"] / row["prefix_doubling_s"]
+            rows.append(row)
+            del arrays, d
+            torch.cuda.empty_cache()
+    if rank != 0:
+        return
+    top = rows[-1]
+    line = {
+        "metric": "suffix-array construction rate", "value": top["dc3_bases_per_s"], "unit": "bases/s",
+        "n_gpus": world, "steps": steps, "warmup": 1, "ms_per_step": top["dc3_s"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64",
+        "data": "synthetic",
+        "config": {"workload": "sa-build-dc3-vs-doubling", "sizes": [r["n"] for r in rows],
+                   "text": "human-like synthetic (GC 0.41, 45% repeat families, 3% tandem repeats)",
+                   "timing": "host wall clock around one synchronous call, text resident on the device"},
+        "rows": rows, "all_equal": all(r["equal"] for r in rows), "clocks": clk.summary(),
+    }
     print(json.dumps(line), flush=True)
 
 
@@ -1168,7 +1264,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=6.0)
     ap.add_argument("--workload", choices=["human-sized", "repetitive-100m", "plain-small", "multi-genome",
-                                           "serving", "paper-shaped"],
+                                           "serving", "paper-shaped", "build"],
                     default="human-sized")
     ap.add_argument("--autotune", action="store_true", help="tune the launch shape before timing (human-sized)")
     ap.add_argument("--order", choices=["auto", "kmer", "input"], default="auto",
@@ -1197,6 +1293,8 @@ def main():
         run_human_sized(args, world, rank, local)
     elif args.workload == "paper-shaped":
         run_paper_shaped(args, world, rank, local)
+    elif args.workload == "build":
+        run_build(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 

@@ -144,13 +144,13 @@ __global__ void bucket_scan_kernel(const __grid_constant__ SearchLaunch a) {
 // written straight to its slot from each lane would put the 32 lanes of a
 // warp in 32 different runs).
 constexpr int kScatterThreads = 256;
-constexpr int kScatterItems = 4;
-constexpr uint32_t kScatterTile = (uint32_t)kScatterThreads * kScatterItems;  // 64 KB of records
+constexpr int kScatterItems = 2;
+constexpr uint32_t kScatterTile = (uint32_t)kScatterThreads * kScatterItems;  // 32 KB of records
 constexpr size_t kScatterSmem = (size_t)kScatterTile * 64;
 
 template <bool kSingle>
-__global__ void __launch_bounds__(kScatterThreads) bucket_scatter_kernel(const __grid_constant__ SearchLaunch a,
-                                                                        uint4 *__restrict__ list) {
+__global__ void __launch_bounds__(kScatterThreads, 5) bucket_scatter_kernel(const __grid_constant__ SearchLaunch a,
+                                                                           uint4 *__restrict__ list) {
     extern __shared__ uint4 srec[];  // kScatterTile records of 4 uint4
     __shared__ uint32_t cnt[kNumBuckets + 1];
     __shared__ uint32_t off[kNumBuckets + 1];
@@ -158,16 +158,38 @@ __global__ void __launch_bounds__(kScatterThreads) bucket_scatter_kernel(const _
     __shared__ uint16_t slot_bucket[kScatterTile];
     __shared__ uint32_t n_valid;
     for (unsigned i = threadIdx.x; i <= kNumBuckets; i += blockDim.x) cnt[i] = 0;
-    __syncthreads();
     const uint64_t tile = (uint64_t)blockIdx.x * kScatterTile;
     uint16_t b[kScatterItems];
-    uint32_t rank[kScatterItems];
+    uint32_t rank[kScatterItems], r[kScatterItems], m[kScatterItems];
+    uint64_t qa[kScatterItems], w[kScatterItems][4];
+    // Every item's loads are issued before the tile's bookkeeping, so that
+    // their DRAM round trips overlap each other and the scans below.
 #pragma unroll
     for (int it = 0; it < kScatterItems; it++) {
         const uint64_t q = tile + (uint64_t)it * kScatterThreads + threadIdx.x;
         b[it] = q < a.n_q ? a.qbucket[q] : kNoQuery;
-        rank[it] = b[it] != kNoQuery ? atomicAdd(&cnt[b[it]], 1u) : 0u;
+        r[it] = kSingle || b[it] == kNoQuery ? 0u : __ldg(a.q_ref + q);
     }
+#pragma unroll
+    for (int it = 0; it < kScatterItems; it++) {
+        const uint64_t q = tile + (uint64_t)it * kScatterThreads + threadIdx.x;
+        qa[it] = 0;
+        m[it] = 0;
+        if (b[it] != kNoQuery) {
+            bool bad_range, bad_ref;
+            query_range(a, q, &r[it], &qa[it], &m[it], &bad_range, &bad_ref);
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < kScatterItems; it++) {
+        // a query without a record reads the batch's first words (always there)
+        const bool live = b[it] != kNoQuery;
+        load_query_head(a.tq, a.tv, live ? qa[it] >> 5 : 0, live ? (uint32_t)(qa[it] & 31u) : 0u, m[it], false,
+                        w[it]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kScatterItems; it++) rank[it] = b[it] != kNoQuery ? atomicAdd(&cnt[b[it]], 1u) : 0u;
     __syncthreads();
     // the tile's runs: exclusive scan of its counts (first warp), and each
     // run's place in the list, reserved with one atomic per bucket
@@ -191,27 +213,22 @@ __global__ void __launch_bounds__(kScatterThreads) bucket_scatter_kernel(const _
     for (unsigned i = threadIdx.x; i <= kNumBuckets; i += blockDim.x)
         base[i] = cnt[i] ? atomicAdd(a.bcursor + i, cnt[i]) : 0u;
     __syncthreads();
-#pragma unroll 1
+#pragma unroll
     for (int it = 0; it < kScatterItems; it++) {
         if (b[it] == kNoQuery) continue;
         const uint64_t q = tile + (uint64_t)it * kScatterThreads + threadIdx.x;
-        uint32_t r = kSingle ? 0u : __ldg(a.q_ref + q);
-        uint64_t qa;
-        uint32_t m;
-        bool bad_range, bad_ref;
-        query_range(a, q, &r, &qa, &m, &bad_range, &bad_ref);
-        uint64_t w[4];
-        load_query_head(a.tq, a.tv, qa >> 5, (uint32_t)(qa & 31u), m, false, w);
         const bool entry = b[it] < kNumBuckets;
-        const uint32_t n = (uint32_t)a.refs.r[kSingle ? 0u : r].n;
+        const uint32_t n = (uint32_t)a.refs.r[kSingle ? 0u : r[it]].n;
         const uint32_t slot = off[b[it]] + rank[it];
         uint4 *dst = srec + 4 * slot;
         // bracket (-1, n) for a query without a k-mer bracket; an entry
         // record's bracket comes from its k-mer entry
-        dst[0] = make_uint4(0xFFFFFFFFu, entry ? 0u : n, m, (uint32_t)q);
-        dst[1] = make_uint4(r, entry ? kRecNeedsEntry : 0u, (uint32_t)qa, (uint32_t)(qa >> 32));
-        dst[2] = make_uint4((uint32_t)w[0], (uint32_t)(w[0] >> 32), (uint32_t)w[1], (uint32_t)(w[1] >> 32));
-        dst[3] = make_uint4((uint32_t)w[2], (uint32_t)(w[2] >> 32), (uint32_t)w[3], (uint32_t)(w[3] >> 32));
+        dst[0] = make_uint4(0xFFFFFFFFu, entry ? 0u : n, m[it], (uint32_t)q);
+        dst[1] = make_uint4(r[it], entry ? kRecNeedsEntry : 0u, (uint32_t)qa[it], (uint32_t)(qa[it] >> 32));
+        dst[2] = make_uint4((uint32_t)w[it][0], (uint32_t)(w[it][0] >> 32), (uint32_t)w[it][1],
+                            (uint32_t)(w[it][1] >> 32));
+        dst[3] = make_uint4((uint32_t)w[it][2], (uint32_t)(w[it][2] >> 32), (uint32_t)w[it][3],
+                            (uint32_t)(w[it][3] >> 32));
         slot_bucket[slot] = b[it];
     }
     __syncthreads();

@@ -15,10 +15,12 @@
 //      (Section III's B0 example: S9 <= S0 <= S6 <= S3): the mod-1 samples in
 //      rank order give them sorted by the second key, and a stable radix sort
 //      by the letter finishes;
-//   4. the two sorted lists are merged (merge path: each thread finds where
-//      its run of outputs starts by a binary search on its diagonal, then
-//      merges the run); a mod-0 suffix and a sample compare by at most two
-//      letters and one sample rank.
+//   4. the two sorted lists are merged: a mod-0 suffix and a sample compare
+//      by at most two letters and one sample rank, so each suffix's key (two
+//      letters, two ranks) is gathered once into a 16-byte record in list
+//      order, and the merge streams the records (merge path: each thread
+//      finds where its run of 32 outputs starts by a binary search on its
+//      diagonal, then merges the run).
 // The radix sorts, scans and compactions come from CUB; the rest are kernels
 // here.  The top level reads its letters (codes 1..4, 0 past the end) from the
 // packed text, so the text is never unpacked.
@@ -122,47 +124,71 @@ __global__ void mod0_candidates_kernel(const uint32_t *__restrict__ s12, uint64_
 }
 
 // The merge of the mod-0 list A and the sample list B (without the empty
-// sample).  before(a, b): is mod-0 suffix a before sample suffix b?
+// sample).  A mod-0 suffix a and a sample b compare by at most two letters and
+// one sample rank: a's key is {s(a), s(a+1), rank(a+1), rank(a+2)}; a mod-1
+// sample's {s(b), -, rank(b+1), -}; a mod-2 sample's {s(b), s(b+1), -,
+// rank(b+2)} (the rank of the suffix past the end is 0, below every sample).
+// The keys are gathered once (merge_keys_kernel: the random reads of the
+// merge), so that the merge itself streams them.
 template <typename L>
-struct Before {
+struct KeyOf {
     L s;
     const uint32_t *red;  // 1-based sample ranks
     uint64_t n, n0;
-    __device__ __forceinline__ uint32_t rank(uint64_t p) const { return p >= n ? 0u : red[ridx(p, n0)]; }
-    __device__ __forceinline__ bool operator()(uint64_t a, uint64_t b) const {
-        const uint32_t sa = s(a), sb = s(b);
-        if (sa != sb) return sa < sb;
-        if (b % 3 == 1) return rank(a + 1) < rank(b + 1);
-        const uint32_t sa1 = s(a + 1), sb1 = s(b + 1);
-        if (sa1 != sb1) return sa1 < sb1;
-        return rank(a + 2) < rank(b + 2);
+    __device__ __forceinline__ uint32_t rank(uint64_t p) const { return p >= n ? 0u : __ldg(red + ridx(p, n0)); }
+    __device__ __forceinline__ uint4 operator()(uint64_t p) const {
+        const uint32_t m = (uint32_t)(p % 3);
+        return make_uint4(s(p), m == 1 ? 0u : s(p + 1), m == 2 ? 0u : rank(p + 1), m == 1 ? 0u : rank(p + 2));
     }
 };
 
-constexpr int kMergeItems = 8;
-
 template <typename L>
-__global__ void merge_kernel(Before<L> before, const uint32_t *__restrict__ A, uint64_t na,
-                             const uint32_t *__restrict__ B, uint64_t nb, uint32_t *out) {
+__global__ void merge_keys_kernel(KeyOf<L> key, const uint32_t *__restrict__ P, uint64_t np, uint4 *K) {
+    DC3_LOOP(i, np) K[i] = key(__ldg(P + i));
+}
+
+// Is the mod-0 suffix with key ka before the sample with key kb (kb_mod1: the
+// sample is a mod-1 one)?
+__device__ __forceinline__ bool key_before(uint4 ka, uint4 kb, bool kb_mod1) {
+    if (ka.x != kb.x) return ka.x < kb.x;
+    if (kb_mod1) return ka.z < kb.z;
+    if (ka.y != kb.y) return ka.y < kb.y;
+    return ka.w < kb.w;
+}
+
+constexpr int kMergeItems = 32;
+
+__global__ void merge_kernel(const uint4 *__restrict__ KA, const uint32_t *__restrict__ A, uint64_t na,
+                             const uint4 *__restrict__ KB, const uint32_t *__restrict__ B, uint64_t nb,
+                             uint32_t *out) {
     const uint64_t total = na + nb;
     DC3_LOOP(tid, (total + kMergeItems - 1) / kMergeItems) {
         const uint64_t d = tid * kMergeItems;
         // co-rank: how many of the first d outputs come from A
         uint64_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
         while (lo < hi) {
-            const uint64_t i = (lo + hi) / 2;
-            if (before(A[i], B[d - i - 1]))
+            const uint64_t i = (lo + hi) / 2, j = d - i - 1;
+            if (key_before(__ldg(KA + i), __ldg(KB + j), __ldg(B + j) % 3 == 1))
                 lo = i + 1;
             else
                 hi = i;
         }
         uint64_t i = lo, j = d - lo;
         const uint64_t end = d + kMergeItems < total ? d + kMergeItems : total;
+        uint4 ka = i < na ? __ldg(KA + i) : make_uint4(0, 0, 0, 0);
+        uint4 kb = j < nb ? __ldg(KB + j) : make_uint4(0, 0, 0, 0);
+        uint32_t pb = j < nb ? __ldg(B + j) : 0u;
         for (uint64_t o = d; o < end; o++) {
-            if (j >= nb || (i < na && before(A[i], B[j])))
-                out[o] = A[i++];
-            else
-                out[o] = B[j++];
+            if (j >= nb || (i < na && key_before(ka, kb, pb % 3 == 1))) {
+                out[o] = __ldg(A + i);
+                if (++i < na) ka = __ldg(KA + i);
+            } else {
+                out[o] = pb;
+                if (++j < nb) {
+                    kb = __ldg(KB + j);
+                    pb = __ldg(B + j);
+                }
+            }
         }
     }
 }
@@ -330,9 +356,18 @@ int skew_gpu(L s, uint64_t n, uint32_t K, uint32_t *sa, cudaStream_t st) {
 
     // Step 4: merge (the empty sample, rank 1, is dropped from the front).
     const uint64_t skip = (n0 > (n + 1) / 3) ? 1 : 0;
-    Before<L> before{s, red, n, n0};
-    const uint64_t blocks_of = (n + kMergeItems - 1) / kMergeItems;
-    merge_kernel<<<grid_of(blocks_of), kThreads, 0, st>>>(before, mod0, n0, s12 + skip, n02 - skip, sa);
+    sc.release(flag);
+    sc.release(k0);
+    sc.release(k1);
+    uint4 *KA = sc.get<uint4>(n0), *KB = sc.get<uint4>(n02);
+    if (sc.failed) return SA_ERR_NOMEM;
+    const KeyOf<L> key{s, red, n, n0};
+    merge_keys_kernel<<<grid_of(n0), kThreads, 0, st>>>(key, mod0, n0, KA);
+    DC3_CK(cudaGetLastError());
+    merge_keys_kernel<<<grid_of(n02 - skip), kThreads, 0, st>>>(key, s12 + skip, n02 - skip, KB);
+    DC3_CK(cudaGetLastError());
+    const uint64_t threads_of = (n + kMergeItems - 1) / kMergeItems;
+    merge_kernel<<<grid_of(threads_of), kThreads, 0, st>>>(KA, mod0, n0, KB, s12 + skip, n02 - skip, sa);
     DC3_CK(cudaGetLastError());
     DC3_CK(cudaStreamSynchronize(st));
     return SA_OK;
