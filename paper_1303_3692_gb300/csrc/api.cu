@@ -776,11 +776,23 @@ int search_pipelined(const sa_index *const *refs, uint32_t n_refs, uint32_t widt
                      const uint64_t *q_offsets, const uint32_t *q_ref, uint64_t n_q, sa_result *out,
                      cudaStream_t s, const sa_search_params *params, bool locate, uint32_t cap,
                      uint64_t *out_offsets, void *out_pos, uint64_t capacity) {
+    // Chunks of about n_q / 12 queries (at least 2^20); the last such chunk's
+    // queries go in four quarter chunks, so that less work is left after the
+    // final upload.
     const uint64_t per = (n_q + 11) / 12 > (1ull << 20) ? (n_q + 11) / 12 : (1ull << 20);
-    const uint64_t n_chunks = (n_q + per - 1) / per;
+    std::vector<uint64_t> cut;  // chunk c is [cut[c], cut[c + 1])
+    try {
+        cut.push_back(0);
+        while (n_q - cut.back() > per) cut.push_back(cut.back() + per);
+        const uint64_t rest = n_q - cut.back(), quarter = (rest + 3) / 4;
+        for (int j = 0; j < 4 && cut.back() < n_q; j++) cut.push_back(cut.back() + quarter < n_q ? cut.back() + quarter : n_q);
+    } catch (const std::bad_alloc &) {
+        return SA_ERR_NOMEM;
+    }
+    const uint64_t n_chunks = cut.size() - 1;
     uint64_t max_bases = 0;
     for (uint64_t c = 0; c < n_chunks; c++) {
-        const uint64_t a = c * per, b = a + per < n_q ? a + per : n_q;
+        const uint64_t a = cut[c], b = cut[c + 1];
         if (q_offsets[b] < q_offsets[a]) return SA_ERR_ARG;
         if (q_offsets[b] - q_offsets[a] > max_bases) max_bases = q_offsets[b] - q_offsets[a];
     }
@@ -790,6 +802,18 @@ int search_pipelined(const sa_index *const *refs, uint32_t n_refs, uint32_t widt
     const bool ref_dev = q_ref && on_device(q_ref);
     const bool off_dev = !locate || on_device(out_offsets);
     const bool pos_dev = !locate || out_pos == nullptr || on_device(out_pos);
+    // A host positions array the device can address (pinned or registered)
+    // receives each chunk's positions as soon as its locate is done, instead
+    // of all of them after the last chunk.
+    void *pos_host_dev = nullptr;
+    if (!pos_dev && capacity) {
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, out_pos) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer != nullptr)
+            pos_host_dev = pa.devicePointer;
+        else
+            cudaGetLastError();
+    }
     int *dstatus = params ? params->device_status : nullptr;
     if (dstatus && !on_device(dstatus)) return SA_ERR_ARG;
     sa_search_params cp;  // the caller's knobs, without the per-call extras the chunks do not take
@@ -841,7 +865,7 @@ int search_pipelined(const sa_index *const *refs, uint32_t n_refs, uint32_t widt
         for (uint64_t c = 0; c < n_chunks && st == SA_OK; c++) {
             const int i = (int)(c % kPipelineStreams);
             cudaStream_t t = ts[i];
-            const uint64_t a = c * per, b = a + per < n_q ? a + per : n_q, nq = b - a;
+            const uint64_t a = cut[c], b = cut[c + 1], nq = b - a;
             const uint64_t ba = q_offsets[a], nb = q_offsets[b] - ba;
             if (nb && (err = cudaMemcpyAsync(slot_bases[i], q_bases + ba, nb, cudaMemcpyHostToDevice, t)) != cudaSuccess)
                 break;
@@ -865,6 +889,9 @@ int search_pipelined(const sa_index *const *refs, uint32_t n_refs, uint32_t widt
                                    c ? off_d + a : zero, stat_d + 1, t, csc);
                 if (st) break;
                 if ((err = cudaEventRecord(loc_done[i], t)) != cudaSuccess) break;
+                if (pos_host_dev && (err = launch_copy_positions(off_d + a, off_d + b, pos_d, pos_host_dev, width,
+                                                                 capacity, t)) != cudaSuccess)
+                    break;
                 if (!off_dev && (err = cudaMemcpyAsync(out_offsets + a, off_d + a, nq * 8, cudaMemcpyDeviceToHost,
                                                        t)) != cudaSuccess)
                     break;
@@ -892,7 +919,7 @@ int search_pipelined(const sa_index *const *refs, uint32_t n_refs, uint32_t widt
             if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return status_from_cuda(err);
             if (locate && !off_dev) out_offsets[n_q] = total;
             const uint64_t kept = total < capacity ? total : capacity;
-            if (locate && !pos_dev && pos_d && kept) {
+            if (locate && !pos_dev && pos_d && kept && !pos_host_dev) {
                 if ((err = cudaMemcpyAsync(out_pos, pos_d, kept * width, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
                     return status_from_cuda(err);
                 if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return status_from_cuda(err);

@@ -206,4 +206,32 @@ cudaError_t launch_locate(const LocateLaunch &L, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+namespace {
+
+// Copies the positions [*first, *last) of one chunk of a batch, clamped to
+// the capacity, from the device array to the caller's host array (host
+// memory the device can address).  The range is known only on the device.
+template <typename IdxT>
+__global__ void copy_positions_kernel(const uint64_t *__restrict__ first, const uint64_t *__restrict__ last,
+                                      const IdxT *__restrict__ src, IdxT *dst, uint64_t capacity) {
+    const uint64_t a = *first < capacity ? *first : capacity;
+    const uint64_t b = *last < capacity ? *last : capacity;
+    for (uint64_t i = a + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += (uint64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+}  // namespace
+
+cudaError_t launch_copy_positions(const uint64_t *first, const uint64_t *last, const void *src, void *dst,
+                                  uint32_t width, uint64_t capacity, cudaStream_t s) {
+    const unsigned blocks = (unsigned)device_sm_count() / 2u + 1u;  // a few SMs: the link is the limit
+    if (width == 4)
+        copy_positions_kernel<uint32_t><<<blocks, 256, 0, s>>>(first, last, reinterpret_cast<const uint32_t *>(src),
+                                                               reinterpret_cast<uint32_t *>(dst), capacity);
+    else
+        copy_positions_kernel<uint64_t><<<blocks, 256, 0, s>>>(first, last, reinterpret_cast<const uint64_t *>(src),
+                                                               reinterpret_cast<uint64_t *>(dst), capacity);
+    return cudaGetLastError();
+}
+
 }  // namespace sa

@@ -452,5 +452,10 @@ uint64_t locate_tiles(uint64_t n_q);
 // device (looked up once per device) and the number of partial sums it holds.
 cudaError_t locate_static_partials(uint64_t **ptr, uint64_t *entries);
 cudaError_t launch_locate(const LocateLaunch &L, cudaStream_t s);
+// Copies positions [*first, *last) (clamped to capacity) of width bytes each
+// from src to dst at the same indexes; dst may be host memory the device can
+// address.
+cudaError_t launch_copy_positions(const uint64_t *first, const uint64_t *last, const void *src, void *dst,
+                                  uint32_t width, uint64_t capacity, cudaStream_t s);
 
 }  // namespace sa

@@ -54,25 +54,40 @@ def test_host_search_equals_device(env, pinned):
         assert out[q, 0] == lo and out[q, 1] == hi
 
 
-def test_host_search_locate_equals_device(env):
+@pytest.mark.parametrize("pinned", [False, True])
+def test_host_search_locate_equals_device(env, pinned):
+    """Pageable buffers get the positions after the last chunk; pinned ones
+    receive each chunk's positions as soon as its locate is done."""
     sa, refs, idxs, qb, qo = env
     cap = 8
     q_ref = (np.arange(N_Q) % 3 == 0).astype(np.uint32)  # two references in one call
     want_r, want_o, want_p = _device(sa, idxs, qb, qo, cap, q_ref)
     total = int(want_o[-1])
-    res = np.empty((N_Q, sa.RESULT_FIELDS), dtype=np.int64)
-    offs = np.empty(N_Q + 1, dtype=np.int64)
-    pos = np.empty(total, dtype=np.int32)
-    sa.sa_search_locate(idxs, qb, qo, cap, q_ref=q_ref, out=res, out_offsets=offs, out_pos=pos, capacity=total)
-    assert np.array_equal(res, want_r)
-    assert np.array_equal(offs, want_o)
-    assert np.array_equal(pos, want_p[:total])
-    # too small a positions buffer: the positions that fit, and SA_ERR_CAPACITY
+
+    def host(shape, dtype):
+        t = torch.empty(shape, dtype=dtype)
+        return t.pin_memory() if pinned else t
+
+    res = host((N_Q, sa.RESULT_FIELDS), torch.int64)
+    offs = host(N_Q + 1, torch.int64)
+    pos = host(total, torch.int32)
+    pos.fill_(-7)
+    qb_h = torch.from_numpy(qb).pin_memory() if pinned else qb
+    qo_h = torch.from_numpy(qo).pin_memory() if pinned else qo
+    sa.sa_search_locate(idxs, qb_h, qo_h, cap, q_ref=q_ref, out=res, out_offsets=offs, out_pos=pos, capacity=total)
+    assert np.array_equal(res.numpy(), want_r)
+    assert np.array_equal(offs.numpy(), want_o)
+    assert np.array_equal(pos.numpy(), want_p[:total])
+    # too small a positions buffer: the positions that fit, nothing past the
+    # capacity, and SA_ERR_CAPACITY
+    pos.fill_(-7)
     with pytest.raises(sa.SAError) as e:
-        sa.sa_search_locate(idxs, qb, qo, cap, q_ref=q_ref, out=res, out_offsets=offs, out_pos=pos,
+        sa.sa_search_locate(idxs, qb_h, qo_h, cap, q_ref=q_ref, out=res, out_offsets=offs, out_pos=pos,
                             capacity=total - 5)
     assert e.value.status == sa.SA_ERR_CAPACITY
-    assert np.array_equal(offs, want_o) and np.array_equal(pos[:total - 5], want_p[:total - 5])
+    p = pos.numpy()
+    assert np.array_equal(offs.numpy(), want_o) and np.array_equal(p[:total - 5], want_p[:total - 5])
+    assert (p[total - 5:] == -7).all()
 
 
 def test_host_pipeline_reports_bad_bases(env):
