@@ -530,7 +530,7 @@ def human_byte_model(T, sa_h, w, k: int, cap: int, sample: int = 20000, seed: in
     rng = np.random.default_rng(seed)
     pick = np.sort(rng.choice(n_q, size=min(sample, n_q), replace=False))
     n = T.size
-    tot = dict(m=0.0, entry=0.0, further=0.0, windows=0.0, kept=0.0, count=0.0)
+    tot = dict(m=0.0, entry=0.0, further=0.0, windows=0.0, kept=0.0, count=0.0, plain_probes=0.0, plain_chunks=0.0)
     for q in pick:
         P = w.q_bases[w.q_offsets[q]:w.q_offsets[q + 1]]
         if P.size >= k:
@@ -540,6 +540,11 @@ def human_byte_model(T, sa_h, w, k: int, cap: int, sample: int = 20000, seed: in
             pr, wi, tr, lo, hi = oracle.probe_model_bracket(T, sa_h, (tlo, thi), P, d0=13)
         else:
             pr, wi, tr, lo, hi = oracle.probe_model_bracket(T, sa_h, None, P, d0=13)
+        # the plain lockstep search over [-1, n) (no k-mer entries, no records):
+        # probes below depth 13 and the 64-base text chunks they compare
+        pp, pc, _, _ = oracle.probe_model(T, sa_h, P, d0=13)
+        tot["plain_probes"] += pp
+        tot["plain_chunks"] += pc
         tot["m"] += P.size
         tot["entry"] += tr
         # the 64-byte k-mer entry carries the bracket's first pivot: that probe costs no record read
@@ -569,6 +574,10 @@ def human_byte_model(T, sa_h, w, k: int, cap: int, sample: int = 20000, seed: in
         "entry_reads_per_query": per["entry"], "record_probes_per_query": per["further"],
         "text_windows_per_query": per["windows"], "mean_count": per["count"], "mean_kept": per["kept"],
         "reorder_bytes_per_query": reorder, "order": "kmer" if kmer_order else "input",
+        # packed query + 32 B per probe and per text chunk + 20 B of result + 8 B per kept position
+        "plain_lockstep_bytes_per_query": m / 4 + 32 * (per["plain_probes"] + per["plain_chunks"]) + 20
+                                          + 8 * per["kept"],
+        "plain_lockstep_probes_per_query": per["plain_probes"],
         "source": "oracle.probe_model_bracket over the oracle-verified suffix array",
     }
 
@@ -780,6 +789,15 @@ def run_human_sized(args, world, rank, local):
                                  "ceilings_G_reads_per_s": ceiling,
                                  "peak_source": "sa_random_read_rate_ex(size, 1024 threads/SM, 64 dependent reads)"},
                 "model": model}
+        # For context: the bytes the plain lockstep search would move (every probe
+        # below depth 13 a 32-byte read plus 32 bytes per 64-base text chunk it
+        # compares), over the whole step's time.  The k-mer entries and records
+        # exist to avoid most of them, so this is not the kernel's own roofline.
+        pb = model["plain_lockstep_bytes_per_query"]
+        step_s = total_s / args.steps
+        roof["plain_lockstep_model"] = {"bytes_per_query": pb, "probes_per_query": model["plain_lockstep_probes_per_query"],
+                                        "achieved_gbs": pb * n_q / step_s / 1e9,
+                                        "frac": pb * n_q / step_s / 1e9 / peak, "over": "whole step"}
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             cpu = cpu_baseline_sa(T, sa_h, w, args, f"oracle-verified GPU suffix array ({verify_s:.1f} s to verify)")
