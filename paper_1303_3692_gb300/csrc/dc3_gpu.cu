@@ -109,9 +109,10 @@ __global__ void ranks_of_kernel(const uint32_t *__restrict__ sar, uint64_t m, ui
     DC3_LOOP(r, m) red[sar[r]] = (uint32_t)(r + 1);
 }
 
-// s12[red[j] - 1] = position of sample j: the samples in rank order.
-__global__ void samples_in_order_kernel(const uint32_t *__restrict__ red, uint64_t n0, uint64_t n02, uint32_t *s12) {
-    DC3_LOOP(j, n02) s12[red[j] - 1] = (uint32_t)sample_pos(j, n0);
+// s12[r] = position of the sample at rank r + 1, read off the reduced
+// string's suffix array (whose r-th entry is that sample's index).
+__global__ void samples_in_order_kernel(const uint32_t *__restrict__ sar, uint64_t n0, uint64_t n02, uint32_t *s12) {
+    DC3_LOOP(r, n02) s12[r] = (uint32_t)sample_pos(__ldg(sar + r), n0);
 }
 
 // The predecessors of the mod-1 samples, in the samples' rank order.
@@ -311,24 +312,28 @@ int skew_gpu(L s, uint64_t n, uint32_t K, uint32_t *sa, cudaStream_t st) {
     uint32_t names = 0;
     DC3_CK(cudaMemcpyAsync(&names, other + (n02 - 1), sizeof names, cudaMemcpyDeviceToHost, st));
     DC3_CK(cudaStreamSynchronize(st));
-    sc.release(posA);
-    sc.release(posB);
+    uint32_t *s12 = nullptr;  // the sample positions in rank order
     if (names < n02) {
         // equal triples: the reduced string's suffix array orders the samples
+        sc.release(posA);
+        sc.release(posB);
         uint32_t *sar = sc.get<uint32_t>(n02);
         if (!sar) return SA_ERR_NOMEM;
         int r = skew_gpu(NameLetters{red, n02}, n02, names, sar, st);
         if (r) return r;
         ranks_of_kernel<<<grid_of(n02), kThreads, 0, st>>>(sar, n02, red);
         DC3_CK(cudaGetLastError());
+        s12 = sc.get<uint32_t>(n02);
+        if (!s12) return SA_ERR_NOMEM;
+        samples_in_order_kernel<<<grid_of(n02), kThreads, 0, st>>>(sar, n0, n02, s12);
+        DC3_CK(cudaGetLastError());
         sc.release(sar);
+    } else {
+        // every name distinct: it is its sample's rank, and the triple order
+        // is the rank order
+        s12 = sorted;
+        sc.release(other);
     }
-    // otherwise each name already is its sample's rank
-
-    uint32_t *s12 = sc.get<uint32_t>(n02);
-    if (!s12) return SA_ERR_NOMEM;
-    samples_in_order_kernel<<<grid_of(n02), kThreads, 0, st>>>(red, n0, n02, s12);
-    DC3_CK(cudaGetLastError());
 
     // Step 3: the mod-0 suffixes.
     uint32_t *cand = sc.get<uint32_t>(n02), *t0 = sc.get<uint32_t>(n0), *s0 = sc.get<uint32_t>(n0);
