@@ -263,7 +263,8 @@ int search_device(const sa_index *const *refs, uint32_t n_refs, uint32_t width, 
     uint64_t ktotal = 0;
     for (uint32_t r = 0; r < n_refs; r++)
         if (refs[r]->krt) ktotal += 1ull << (2 * refs[r]->kmer_k);
-    const bool kmer_order = !plain && use_kmer_order(refs, n_refs, n_q, order);
+    // (a list record holds a query's first base in 48 bits)
+    const bool kmer_order = !plain && use_kmer_order(refs, n_refs, n_q, order) && tq_words * 32 < kListMaxBase;
     uint16_t *qbucket = kmer_order ? sc.get<uint16_t>(n_q) : nullptr;
     uint4 *wrec_in = kmer_order ? sc.get<uint4>(4 * n_q) : nullptr;
     uint32_t *bh = kmer_order ? sc.get<uint32_t>(2 * (kNumBuckets + 1)) : nullptr;

@@ -27,7 +27,7 @@
 //   bucket_scatter_kernel  per tile of queries, each bucket's run reserved at
 //                          once and every query's 64-byte record (length,
 //                          index, reference, first base in the packed batch,
-//                          first 128 bases; flagged when it has a k-mer
+//                          first 192 bases; flagged when it has a k-mer
 //                          bracket to read) put at its slot, through shared
 //                          memory so that the runs are stored coalesced.
 // The first pass and then the persistent kernel of search.cu take the queries
@@ -218,17 +218,25 @@ __global__ void __launch_bounds__(kScatterThreads, 5) bucket_scatter_kernel(cons
         if (b[it] == kNoQuery) continue;
         const uint64_t q = tile + (uint64_t)it * kScatterThreads + threadIdx.x;
         const bool entry = b[it] < kNumBuckets;
-        const uint32_t n = (uint32_t)a.refs.r[kSingle ? 0u : r[it]].n;
         const uint32_t slot = off[b[it]] + rank[it];
+        // bases 128-191 (the first pass then reads none of a query of up to
+        // 192 bases from the batch; the words are in L1 or L2 from the loads above)
+        uint64_t t0 = 0, t1 = 0;
+        if (m[it] > 128u) {
+            const uint64_t wl = qa[it] >> 5;
+            const uint32_t sh = (uint32_t)(qa[it] & 31u) * 2u;
+            const uint64_t x4 = __ldg(a.tq + wl + 4), x5 = __ldg(a.tq + wl + 5), x6 = __ldg(a.tq + wl + 6);
+            t0 = (x4 << sh) | ((x5 >> 1) >> (63u - sh));
+            t1 = (x5 << sh) | ((x6 >> 1) >> (63u - sh));
+        }
         uint4 *dst = srec + 4 * slot;
-        // bracket (-1, n) for a query without a k-mer bracket; an entry
-        // record's bracket comes from its k-mer entry
-        dst[0] = make_uint4(0xFFFFFFFFu, entry ? 0u : n, m[it], (uint32_t)q);
-        dst[1] = make_uint4(r[it], entry ? kRecNeedsEntry : 0u, (uint32_t)qa[it], (uint32_t)(qa[it] >> 32));
-        dst[2] = make_uint4((uint32_t)w[it][0], (uint32_t)(w[it][0] >> 32), (uint32_t)w[it][1],
+        dst[0] = make_uint4(m[it], (uint32_t)q, (uint32_t)qa[it],
+                            (uint32_t)(qa[it] >> 32) | (r[it] << 16) | (entry ? kListNeedsEntry : 0u));
+        dst[1] = make_uint4((uint32_t)w[it][0], (uint32_t)(w[it][0] >> 32), (uint32_t)w[it][1],
                             (uint32_t)(w[it][1] >> 32));
-        dst[3] = make_uint4((uint32_t)w[it][2], (uint32_t)(w[it][2] >> 32), (uint32_t)w[it][3],
+        dst[2] = make_uint4((uint32_t)w[it][2], (uint32_t)(w[it][2] >> 32), (uint32_t)w[it][3],
                             (uint32_t)(w[it][3] >> 32));
+        dst[3] = make_uint4((uint32_t)t0, (uint32_t)(t0 >> 32), (uint32_t)t1, (uint32_t)(t1 >> 32));
         slot_bucket[slot] = b[it];
     }
     __syncthreads();

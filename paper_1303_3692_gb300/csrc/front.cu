@@ -35,27 +35,62 @@ struct FrontDesc {
     uint32_t kmer_k;
 };
 
-// P (bases 0-127 in w, the rest at base qa of the packed batch; length m >=
-// 1) against the pivot of a k-mer entry: its first 192 bases in e (clamp of
-// them exist), then the text from position pos + 192 when all 192 tie.
+// The query's 32-base window at base `off` (a multiple of 32) past its first
+// 96 bases: base 96 from w3 (the query's fourth word), bases 128-191 from the
+// last 16 bytes of its record in the k-mer-ordered list when there is one (the
+// record just read, instead of a random read into the batch), the rest from
+// the packed batch.
+struct QueryWindows {
+    const uint64_t *tq;
+    uint64_t qa;
+    uint64_t w3;
+    const uint64_t *tail;  // bases 128-159 and 160-191, or null
+    __device__ __forceinline__ uint64_t operator()(uint32_t off) const {
+        if (off == 96u) return w3;
+        if (tail != nullptr && off >= 128u && off < 192u) return __ldg(tail + ((off - 128u) >> 5));
+        return text_window(tq, qa + off);
+    }
+};
+
+// P (length m >= 1; windows from qw) against the suffix at p of a text of n
+// < 2^32 bases, from the 32-aligned base below `start` (< m; all bases before
+// it are known equal).
+__device__ __forceinline__ int cmp_suffix_qw(const uint64_t *__restrict__ T, uint32_t n, uint32_t p,
+                                             const QueryWindows &qw, uint32_t m, uint32_t start, uint32_t *lcp) {
+    uint32_t off = start & ~31u;
+    const uint32_t rem = n - p;
+    for (;;) {
+        const uint32_t qlen = min(32u, m - off);
+        const uint32_t tlen = off < rem ? min(32u, rem - off) : 0u;
+        const uint64_t q = qw(off);
+        const uint64_t t = tlen ? text_window(T, (uint64_t)(p + off)) : 0ull;
+        const int c = cmp_window(q, t, qlen, tlen, off, m, lcp);
+        if (c != 2) return c;
+        off += 32u;
+    }
+}
+
+// P (bases 0-127 in w, the rest from qw; length m >= 1) against the pivot of
+// a k-mer entry: its first 192 bases in e (clamp of them exist), then the
+// text from position pos + 192 when all 192 tie.
 __device__ __forceinline__ int cmp_entry(const uint64_t w[4], uint32_t m, const uint64_t e[6], uint32_t pos,
                                          uint32_t clamp, uint32_t n, const uint64_t *__restrict__ T,
-                                         const uint64_t *__restrict__ tq, uint64_t qa, uint32_t *lcp) {
+                                         const QueryWindows &qw, uint32_t *lcp) {
 #pragma unroll
     for (int j = 0; j < 6; j++) {
         const uint32_t off = 32u * j;
         const uint32_t qlen = min(32u, m - off);
         const uint32_t tlen = clamp > off ? min(32u, clamp - off) : 0u;
-        const uint64_t q = j < 4 ? w[j] : text_window(tq, qa + off);
+        const uint64_t q = j < 4 ? w[j] : qw(off);
         const int c = cmp_window(q, e[j], qlen, tlen, off, m, lcp);
         if (c != 2) return c;
     }
-    return cmp_suffix_tq(T, n, pos, tq, qa, m, 192u, lcp);
+    return cmp_suffix_qw(T, n, pos, qw, m, 192u, lcp);
 }
 
 // kFromList: the queries come from the k-mer-ordered list of bucket.cu (one
 // 64-byte record each: length, index, reference, first base in the packed
-// batch and first 128 bases, already checked) instead of the batch's offsets.
+// batch and first 192 bases, already checked) instead of the batch's offsets.
 template <bool kSingle, bool kFromList>
 __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_constant__ SearchLaunch a) {
     __shared__ FrontDesc sdesc[SA_MAX_REFS];
@@ -109,15 +144,15 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
             const uint4 *src = a.wrec_in + 4 * (size_t)(base + lane);
             ldg32_if(live, src, &c0, &c1);
             ldg32_if(live, src + 2, &c2, &c3);
-            q = c0.w;
-            m = c0.z;
-            r = c1.x;
-            entry = (c1.y & kRecNeedsEntry) != 0u;
-            qa = ((uint64_t)c1.w << 32) | c1.z;
-            w[0] = ((uint64_t)c2.y << 32) | c2.x;
-            w[1] = ((uint64_t)c2.w << 32) | c2.z;
-            w[2] = ((uint64_t)c3.y << 32) | c3.x;
-            w[3] = ((uint64_t)c3.w << 32) | c3.z;
+            m = c0.x;
+            q = c0.y;
+            qa = ((uint64_t)(c0.w & 0xFFFFu) << 32) | c0.z;
+            r = (c0.w >> 16) & 0x7FFFu;
+            entry = (c0.w & kListNeedsEntry) != 0u;
+            w[0] = ((uint64_t)c1.y << 32) | c1.x;
+            w[1] = ((uint64_t)c1.w << 32) | c1.z;
+            w[2] = ((uint64_t)c2.y << 32) | c2.x;
+            w[3] = ((uint64_t)c2.w << 32) | c2.z;
             ok = live;
         } else {
             q = base + lane;
@@ -164,6 +199,11 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
 
         uint32_t lcpL = 0, lcpR = 0, HL = 0, HR = 0, hlcpL = 0, hlcpR = 0, lo = 0, phase = 0;
         bool go = !done && look;
+        // in list order, bases 128-191 are the record's last 16 bytes (read
+        // again when a compare gets there: an L1 or L2 hit)
+        const QueryWindows qw{tq, qa, w[3],
+                              kFromList ? reinterpret_cast<const uint64_t *>(a.wrec_in + 4 * (size_t)(base + lane) + 3)
+                                        : nullptr};
         // One compare's outcome c at pivot M with common prefix l.
         auto step = [&](int c, uint32_t M, uint32_t l) {
             if (c == CMP_PREFIX && phase == 0) {
@@ -202,7 +242,7 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
                                    ((uint64_t)e23.y << 32) | e23.x, ((uint64_t)e23.w << 32) | e23.z,
                                    ((uint64_t)e45.y << 32) | e45.x, ((uint64_t)e45.w << 32) | e45.z};
             uint32_t l;
-            const int c = cmp_entry(w, m, e, h.z, h.w, d.n, d.text, tq, qa, &l);
+            const int c = cmp_entry(w, m, e, h.z, h.w, d.n, d.text, qw, &l);
             step(c, L + ((R - L) >> 1), l);
         }
         // Further probes, one suffix record each; queries without a k-mer
@@ -216,7 +256,7 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
                 uint32_t l;
                 bool und = false;
                 int c = cmp_record(w[0], w[1], w[2], w[3], m, r0, r1, d.n, &l, &und);
-                if (und) c = cmp_suffix_tq(d.text, d.n, r1.w, tq, qa, m, max(112u, min(lcpL, lcpR)), &l);
+                if (und) c = cmp_suffix_qw(d.text, d.n, r1.w, qw, m, max(112u, min(lcpL, lcpR)), &l);
                 step(c, M, l);
             }
         }

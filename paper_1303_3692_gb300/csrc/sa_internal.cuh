@@ -48,6 +48,14 @@ struct RefDesc {
 constexpr uint32_t kNumBuckets = 256;
 // Worklist record flag ({ref, flags, qa}): read the query's k-mer entry first.
 constexpr uint32_t kRecNeedsEntry = 1u;
+// The k-mer-ordered list's 64-byte records (bucket.cu writes, front.cu reads):
+//   {m, q, qa.lo, qa.hi | ref << 16 | kListNeedsEntry}  length, index, first
+//       base in the packed batch (qa < 2^48), reference id (< 2^15), and
+//       whether the query has a k-mer bracket to read
+//   {w0, w1}, {w2, w3}, {w4, w5}  its first 192 bases as packed words (the
+//       words past the query's end are not its bases)
+constexpr uint32_t kListNeedsEntry = 0x80000000u;
+constexpr uint64_t kListMaxBase = 1ull << 48;
 
 // The compare outcome of the three cases of Section IV.
 enum : int { CMP_LESS = -1, CMP_PREFIX = 0, CMP_GREATER = 1 };
