@@ -257,14 +257,16 @@ int search_device(const sa_index *const *refs, uint32_t n_refs, uint32_t width, 
     const uint64_t nwords = (total + 31) / 32;
     // both packings, one after the other, when each query names its strand
     const uint64_t tq_words = (nwords + SA_TQ_PAD_WORDS) * (strand_bits ? 2 : 1);
+    // list and worklist records hold a query's first base in 48 bits (a batch
+    // that large could not be resident anyway)
+    if (!plain && tq_words * 32 >= kListMaxBase) return SA_ERR_ARG;
     uint64_t *tq = sc.get<uint64_t>(tq_words);
     uint32_t *tv = sc.get<uint32_t>(tq_words);
     uint4 *wrec = plain ? nullptr : sc.get<uint4>(4 * n_q);
     uint64_t ktotal = 0;
     for (uint32_t r = 0; r < n_refs; r++)
         if (refs[r]->krt) ktotal += 1ull << (2 * refs[r]->kmer_k);
-    // (a list record holds a query's first base in 48 bits)
-    const bool kmer_order = !plain && use_kmer_order(refs, n_refs, n_q, order) && tq_words * 32 < kListMaxBase;
+    const bool kmer_order = !plain && use_kmer_order(refs, n_refs, n_q, order);
     uint16_t *qbucket = kmer_order ? sc.get<uint16_t>(n_q) : nullptr;
     uint4 *wrec_in = kmer_order ? sc.get<uint4>(4 * n_q) : nullptr;
     uint32_t *bh = kmer_order ? sc.get<uint32_t>(2 * (kNumBuckets + 1)) : nullptr;

@@ -18,7 +18,7 @@
 // resolve, a query shorter than k, an index without a k-mer table) is
 // appended to a worklist -- a 64-byte record holding a bracket of both
 // bounds, its length, index, reference, first base in the packed batch and
-// first 128 bases -- which the persistent kernel of search.cu then finishes.
+// first 160 bases -- which the persistent kernel of search.cu then finishes.
 #include "sa_internal.cuh"
 
 namespace sa {
@@ -34,41 +34,6 @@ struct FrontDesc {
     uint32_t n;
     uint32_t kmer_k;
 };
-
-// The query's 32-base window at base `off` (a multiple of 32) past its first
-// 96 bases: base 96 from w3 (the query's fourth word), bases 128-191 from the
-// last 16 bytes of its record in the k-mer-ordered list when there is one (the
-// record just read, instead of a random read into the batch), the rest from
-// the packed batch.
-struct QueryWindows {
-    const uint64_t *tq;
-    uint64_t qa;
-    uint64_t w3;
-    const uint64_t *tail;  // bases 128-159 and 160-191, or null
-    __device__ __forceinline__ uint64_t operator()(uint32_t off) const {
-        if (off == 96u) return w3;
-        if (tail != nullptr && off >= 128u && off < 192u) return __ldg(tail + ((off - 128u) >> 5));
-        return text_window(tq, qa + off);
-    }
-};
-
-// P (length m >= 1; windows from qw) against the suffix at p of a text of n
-// < 2^32 bases, from the 32-aligned base below `start` (< m; all bases before
-// it are known equal).
-__device__ __forceinline__ int cmp_suffix_qw(const uint64_t *__restrict__ T, uint32_t n, uint32_t p,
-                                             const QueryWindows &qw, uint32_t m, uint32_t start, uint32_t *lcp) {
-    uint32_t off = start & ~31u;
-    const uint32_t rem = n - p;
-    for (;;) {
-        const uint32_t qlen = min(32u, m - off);
-        const uint32_t tlen = off < rem ? min(32u, rem - off) : 0u;
-        const uint64_t q = qw(off);
-        const uint64_t t = tlen ? text_window(T, (uint64_t)(p + off)) : 0ull;
-        const int c = cmp_window(q, t, qlen, tlen, off, m, lcp);
-        if (c != 2) return c;
-        off += 32u;
-    }
-}
 
 // P (bases 0-127 in w, the rest from qw; length m >= 1) against the pivot of
 // a k-mer entry: its first 192 bases in e (clamp of them exist), then the
@@ -203,7 +168,8 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
         // again when a compare gets there: an L1 or L2 hit)
         const QueryWindows qw{tq, qa, w[3],
                               kFromList ? reinterpret_cast<const uint64_t *>(a.wrec_in + 4 * (size_t)(base + lane) + 3)
-                                        : nullptr};
+                                        : nullptr,
+                              kFromList ? 2u : 0u};
         // One compare's outcome c at pivot M with common prefix l.
         auto step = [&](int c, uint32_t M, uint32_t l) {
             if (c == CMP_PREFIX && phase == 0) {
@@ -277,7 +243,9 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
             if (rest) {
                 const uint32_t slot = staged + __popc(bal & lanemask_lt);
                 s_stage[wib][slot][0] = make_uint4(phase == 2 ? lo - 1u : L, phase == 1 ? HR : R, m, (uint32_t)q);
-                s_stage[wib][slot][1] = make_uint4(r, 0u, (uint32_t)qa, (uint32_t)(qa >> 32));
+                const uint64_t w4 = m > 128u ? qw(128u) : 0ull;  // bases 128-159 for the persistent pass
+                s_stage[wib][slot][1] =
+                    make_uint4((uint32_t)qa, (uint32_t)(qa >> 32) | (r << 16), (uint32_t)w4, (uint32_t)(w4 >> 32));
                 s_stage[wib][slot][2] =
                     make_uint4((uint32_t)w[0], (uint32_t)(w[0] >> 32), (uint32_t)w[1], (uint32_t)(w[1] >> 32));
                 s_stage[wib][slot][3] =

@@ -46,8 +46,6 @@ struct RefDesc {
 // k-mer order of a batch (bucket.cu): the slices of the k-mer entries of a
 // call's indexes, plus one bucket for queries without a k-mer bracket.
 constexpr uint32_t kNumBuckets = 256;
-// Worklist record flag ({ref, flags, qa}): read the query's k-mer entry first.
-constexpr uint32_t kRecNeedsEntry = 1u;
 // The k-mer-ordered list's 64-byte records (bucket.cu writes, front.cu reads):
 //   {m, q, qa.lo, qa.hi | ref << 16 | kListNeedsEntry}  length, index, first
 //       base in the packed batch (qa < 2^48), reference id (< 2^15), and
@@ -323,6 +321,39 @@ __device__ __forceinline__ int cmp_suffix_tq(const uint64_t *__restrict__ T, uin
     }
 }
 
+// The query's 32-base window at base `off` (a multiple of 32, off >= 96): base
+// 96 from w3 (the query's fourth packed word), bases 128 .. 128 + 32
+// tail_words - 1 from `tail` (later words its record carries, read again from
+// the record when a compare gets there), the rest from the packed batch.
+struct QueryWindows {
+    const uint64_t *tq;
+    uint64_t qa;
+    uint64_t w3;
+    const uint64_t *tail;
+    uint32_t tail_words;
+    __device__ __forceinline__ uint64_t operator()(uint32_t off) const {
+        if (off == 96u) return w3;
+        if (off >= 128u && ((off - 128u) >> 5) < tail_words) return __ldg(tail + ((off - 128u) >> 5));
+        return text_window(tq, qa + off);
+    }
+};
+
+// cmp_suffix_tq with the query's windows from qw (start >= 96).
+__device__ __forceinline__ int cmp_suffix_qw(const uint64_t *__restrict__ T, uint32_t n, uint32_t p,
+                                             const QueryWindows &qw, uint32_t m, uint32_t start, uint32_t *lcp) {
+    uint32_t off = start & ~31u;
+    const uint32_t rem = n - p;
+    for (;;) {
+        const uint32_t qlen = min(32u, m - off);
+        const uint32_t tlen = off < rem ? min(32u, rem - off) : 0u;
+        const uint64_t q = qw(off);
+        const uint64_t t = tlen ? text_window(T, (uint64_t)(p + off)) : 0ull;
+        const int c = cmp_window(q, t, qlen, tlen, off, m, lcp);
+        if (c != 2) return c;
+        off += 32u;
+    }
+}
+
 }  // namespace sa
 
 // ---------------------------------------------------------------------------
@@ -418,7 +449,9 @@ struct SearchLaunch {
 // Worklist record of a query the first pass did not finish (64 bytes):
 //   {L, R, m, q}            a bracket (L, R) holding both bounds (L = -1 is
 //                           0xFFFFFFFF), the length and the query's index
-//   {ref, 0, qa.lo, qa.hi}  its reference and first base in the packed batch
+//   {qa.lo, qa.hi | ref << 16, w4.lo, w4.hi}  its first base in the packed
+//                           batch (qa < 2^48), reference id (< 2^15) and
+//                           bases 128-159
 //   {w0, w1}, {w2, w3}      its first 128 bases (packed words)
 cudaError_t launch_pack_batch(const SearchLaunch &L, uint64_t *tq, uint32_t *tv, cudaStream_t s);
 cudaError_t launch_front(const SearchLaunch &L, cudaStream_t s);

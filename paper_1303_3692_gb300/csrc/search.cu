@@ -146,7 +146,7 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s for the key-table copy
 // independent loads, so that the 32 lanes of a warp wait for one round per
 // iteration (a lane starting a query never holds up the lanes that probe):
 //   init      read the query's worklist record (bracket, length, index,
-//             reference, first base in the packed batch, first 64 bases); a
+//             first base in the packed batch, reference, first 64 bases); a
 //             query with a k-mer bracket probes from it, any other descends
 //             the key table first;
 //   descent   compare with the key of level-order node k in shared memory
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(1024, 1) search_kernel(const __grid_constant__
         if (init) {
             fresh = false;
             qout = r0.w;
-            const uint32_t r = r1.x;
+            const uint32_t r = (r1.y >> 16) & 0x7FFFu;
             if (!kSingle) {
                 const SmemDesc d = sdesc[r < a.n_refs ? r : 0u];
                 T = d.text;
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(1024, 1) search_kernel(const __grid_constant__
                 depth = d.depth;
             }
             m = r0.z;
-            qa = ((uint64_t)r1.w << 32) | r1.z;
+            qa = ((uint64_t)(r1.y & 0xFFFFu) << 32) | r1.x;
             q0 = x2;
             q1 = x3;
             lcpL = lcpR = 0;
@@ -310,7 +310,11 @@ __global__ void __launch_bounds__(1024, 1) search_kernel(const __grid_constant__
         } else {
             bool und = false;
             c = cmp_record(q0, q1, x2, x3, m, r0, r1, n, &l, &und);
-            if (und) c = cmp_suffix_tq(T, n, r1.w, a.tq, qa, m, max(112u, min(lcpL, lcpR)), &l);
+            if (und) {
+                // query bases 96-127 are x3, 128-159 the worklist record's second word pair
+                const QueryWindows qw{a.tq, qa, x3, reinterpret_cast<const uint64_t *>(wrec) + 3, 1u};
+                c = cmp_suffix_qw(T, n, r1.w, qw, m, max(112u, min(lcpL, lcpR)), &l);
+            }
         }
         if (c == CMP_PREFIX && phase == 0) {
             HL = M;
