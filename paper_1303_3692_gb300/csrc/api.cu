@@ -271,7 +271,7 @@ int search_device(const sa_index *const *refs, uint32_t n_refs, uint32_t width, 
     uint4 *wrec_in = kmer_order ? sc.get<uint4>(4 * n_q) : nullptr;
     uint32_t *bh = kmer_order ? sc.get<uint32_t>(2 * (kNumBuckets + 1)) : nullptr;
     // [0] pack error, [1] status, [2] worklist count, [3] bad reference id,
-    // [4] records of the k-mer-ordered list
+    // [4] records of the k-mer-ordered list, [5] a non-base byte in the batch
     int *flags = sc.get<int>(8);
     unsigned long long *counter = sc.get<unsigned long long>(1);
     if (sc.failed) return SA_ERR_NOMEM;
@@ -327,6 +327,7 @@ int search_device(const sa_index *const *refs, uint32_t n_refs, uint32_t width, 
     L.wrec_in = wrec_in;
     L.wl_in_count = reinterpret_cast<uint32_t *>(flags + 4);
     L.bad_ref = flags + 3;
+    L.batch_dirty = flags + 5;
 
     if ((err = launch_pack_batch(L, tq, tv, s)) != cudaSuccess) return status_from_cuda(err);
     cudaEvent_t ev0 = params ? reinterpret_cast<cudaEvent_t>(params->search_events[0]) : nullptr;

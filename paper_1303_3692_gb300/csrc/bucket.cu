@@ -76,6 +76,9 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_count_kernel(const __gr
     }
     __syncthreads();
     bool any_bad = false, any_bad_ref = false;
+    // a batch without a non-base byte needs no validity masks, only each
+    // query's first word for its bucket
+    const bool dirty = a.batch_dirty == nullptr || *a.batch_dirty != 0;
     const uint64_t tile = (uint64_t)blockIdx.x * kBucketTile;
 #pragma unroll 1
     for (int it = 0; it < kBucketItems; it++) {
@@ -88,10 +91,18 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_count_kernel(const __gr
         bool ok = query_range(a, q, &r, &qa, &m, &bad_range, &bad_ref);
         any_bad |= bad_range;
         any_bad_ref |= bad_ref;
-        uint64_t w[4];
-        if (!load_query_head(a.tq, a.tv, ok ? (qa >> 5) : 0, (uint32_t)(qa & 31u), m, ok && m > 0, w)) {
-            ok = false;
-            any_bad = true;
+        uint64_t w0;
+        if (dirty) {
+            uint64_t w[4];
+            if (!load_query_head(a.tq, a.tv, ok ? (qa >> 5) : 0, (uint32_t)(qa & 31u), m, ok && m > 0, w)) {
+                ok = false;
+                any_bad = true;
+            }
+            w0 = w[0];
+        } else {
+            const uint64_t wl = ok ? (qa >> 5) : 0;
+            const uint32_t sh = ok ? (uint32_t)(qa & 31u) * 2u : 0u;
+            w0 = (__ldg(a.tq + wl) << sh) | ((__ldg(a.tq + wl + 1) >> 1) >> (63u - sh));
         }
         uint16_t b = kNoQuery;
         if (!ok) {
@@ -101,7 +112,7 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_count_kernel(const __gr
             if (m == 0) {
                 store_result(a.out, q, 0, d.n, a.trunc_cap);
             } else if (d.kmer_k != 0 && m >= d.kmer_k) {
-                const uint64_t x = w[0] >> (64u - 2u * d.kmer_k);
+                const uint64_t x = w0 >> (64u - 2u * d.kmer_k);
                 b = (uint16_t)(((d.kbase + x) * kNumBuckets) / a.ktotal);
             } else {
                 b = (uint16_t)kNumBuckets;  // no k-mer bracket: the key-table descent

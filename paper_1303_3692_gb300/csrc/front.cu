@@ -89,6 +89,8 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
     bool any_bad = false, any_bad_ref = false;
 
     const uint64_t n_items = kFromList ? (uint64_t)*a.wl_in_count : a.n_q;
+    // a batch without a non-base byte needs no per-query validity check
+    const bool dirty = a.batch_dirty == nullptr || *a.batch_dirty != 0;
     // Offsets and reference of this lane's next query, read one query ahead.
     uint64_t nqa = 0, nqe = 0;
     uint32_t nr = 0;
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
             if (range_ok) qa = strand_start(qa, qe, a.total, rc, a.rc_base);
 
             // First 128 bases and the validity of every base of the query.
-            if (!load_query_head(tq, a.tv, ok ? (qa >> 5) : 0, (uint32_t)(qa & 31u), m, ok && m > 0, w)) {
+            if (!load_query_head(tq, a.tv, ok ? (qa >> 5) : 0, (uint32_t)(qa & 31u), m, ok && m > 0 && dirty, w)) {
                 ok = false;
                 any_bad = true;
             }

@@ -172,21 +172,20 @@ __device__ __forceinline__ uint32_t bit_range(uint32_t lo, uint32_t hi) {
 // hold the batch's next bases), read as five words from word w_lo = qa / 32
 // of tq with the shift of qa % 32.  With check set, returns whether all m
 // bases (from bit qa % 32 of word w_lo on) are marked valid in the per-word
-// masks tv; else returns true without reading past the five words.
+// masks tv; else returns true without reading the masks.
 __device__ __forceinline__ bool load_query_head(const uint64_t *__restrict__ tq, const uint32_t *__restrict__ tv,
                                                 uint64_t w_lo, uint32_t b0, uint32_t m, bool check,
                                                 uint64_t w[4]) {
     const uint32_t sh = b0 * 2u;
     uint64_t t[5];
-    uint32_t v[5];
 #pragma unroll
-    for (int i = 0; i < 5; i++) {
-        t[i] = __ldg(tq + w_lo + i);
-        v[i] = __ldg(tv + w_lo + i);
-    }
+    for (int i = 0; i < 5; i++) t[i] = __ldg(tq + w_lo + i);
 #pragma unroll
     for (int j = 0; j < 4; j++) w[j] = (t[j] << sh) | ((t[j + 1] >> 1) >> (63u - sh));
     if (!check) return true;
+    uint32_t v[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) v[i] = __ldg(tv + w_lo + i);
     uint32_t badbits = 0;
     const uint64_t end = (uint64_t)b0 + m;  // one past the query's last bit, from word w_lo
 #pragma unroll
@@ -429,6 +428,8 @@ struct SearchLaunch {
     uint32_t *wl_in_count;    // k-mer order: records in wrec_in
     sa_result *out;
     int *pack_err;            // device flag: some query had a non-ACGT byte or bad offsets
+    int *batch_dirty;         // device flag set by the packing: some byte of the batch is not a base
+                              // (null: assume so); a clean batch needs no per-query validity check
     int *bad_ref;             // device flag: some query named a reference id >= n_refs
     unsigned long long *counter;
     int *status;
