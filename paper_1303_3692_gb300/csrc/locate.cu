@@ -97,14 +97,20 @@ __global__ void __launch_bounds__(1024) scan_partials_kernel(uint64_t *partials,
 // One CTA per tile of kTile queries; warp w owns the tile's queries
 // [w * 256, w * 256 + 256), lane l its queries w * 256 + i * 32 + l for
 // i < kItems, so every load of results and store of offsets is coalesced.  A
-// first pass sums the lane's items; one exchange of warp totals through
-// shared memory (one barrier) places the warps within the tile; a second pass
-// (whose loads hit the caches) places each item within the warp's run by a
-// warp scan (shuffles), writes its offset and copies its positions.
+// first pass reads the lane's results once and sums its items, keeping each
+// item's count and lower bound in shared memory; one exchange of warp totals
+// (one barrier) places the warps within the tile; a second pass places each
+// item within the warp's run by a warp scan (shuffles), writes its offset and
+// copies its positions.
 template <typename IdxT>
 __global__ void __launch_bounds__(kTileThreads, 3) tile_gather_kernel(const __grid_constant__ LocateLaunch a) {
     constexpr int kWarps = kTileThreads / 32;
     __shared__ uint64_t s_warp[kWarps];
+    // each item's kept count and lower bound from the first pass (32 KB), so
+    // the second pass does not read the results again: at 3.1 Gbp the L2 no
+    // longer holds them by then
+    __shared__ uint32_t s_k[kItems][kTileThreads];
+    __shared__ uint32_t s_lo[kItems][kTileThreads];
     const uint64_t tile_base = (uint64_t)blockIdx.x * kTile;
     const uint64_t ntiles = gridDim.x;
     if (blockIdx.x == ntiles - 1 && threadIdx.x == 0) a.out_offsets[a.n_q] = a.partials[ntiles];
@@ -116,7 +122,15 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_gather_kernel(const __gr
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
         const uint64_t q = warp_base + (uint64_t)i * 32 + lane;
-        if (q < a.n_q) lane_sum += kept(a.res[q], a.cap);
+        uint32_t k = 0, lo = 0xFFFFFFFFu;  // ranks are below 2^32 - 1: 0xFFFFFFFF copies nothing
+        if (q < a.n_q) {
+            const sa_result r = a.res[q];
+            k = (uint32_t)kept(r, a.cap);  // cap is 32-bit
+            if (r.lo < 0xFFFFFFFFull) lo = (uint32_t)r.lo;
+        }
+        s_k[i][threadIdx.x] = k;
+        s_lo[i][threadIdx.x] = lo;
+        lane_sum += k;
     }
     uint64_t tot = lane_sum;
 #pragma unroll
@@ -126,13 +140,12 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_gather_kernel(const __gr
     uint64_t run = a.partials[blockIdx.x];
     for (unsigned w = 0; w < warp; w++) run += s_warp[w];
 
-    // Second pass over the items (their results are cache hits now).
+    // Second pass over the items, from shared memory.
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
         const uint64_t q = warp_base + (uint64_t)i * 32 + lane;
-        sa_result r{0, 0, 0, 0};
-        if (q < a.n_q) r = a.res[q];
-        const uint32_t k = q < a.n_q ? (uint32_t)kept(r, a.cap) : 0u;  // cap is 32-bit
+        const uint32_t k = s_k[i][threadIdx.x];
+        const uint64_t lo = s_lo[i][threadIdx.x];
         uint64_t x = k;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -146,10 +159,10 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_gather_kernel(const __gr
         if (pos == nullptr || k == 0) continue;
         const uint32_t ref = a.q_ref ? (a.q_ref[q] & ~kStrandBit) : 0u;  // bit 31: the strand, not the reference
         const RefDesc &d = a.refs.r[ref < a.n_refs ? ref : 0];
-        const uint64_t kk = (ref < a.n_refs && r.lo <= d.n && k <= d.n - r.lo) ? k : 0;  // never past SA
+        const uint64_t kk = (ref < a.n_refs && lo <= d.n && k <= d.n - lo) ? k : 0;  // never past SA
         const IdxT *sa = reinterpret_cast<const IdxT *>(d.sa);
         for (uint64_t t = 0; t < kk; t++) {
-            if (off + t < a.capacity) pos[off + t] = __ldg(sa + r.lo + t);
+            if (off + t < a.capacity) pos[off + t] = __ldg(sa + lo + t);
         }
         if (a.overflow != nullptr && off + kk > a.capacity) atomicOr(a.overflow, 1);
     }
