@@ -242,7 +242,7 @@ uint32_t fill_ref_table(const sa_index *const *refs, uint32_t n_refs, uint32_t w
 int search_device(const sa_index *const *refs, uint32_t n_refs, uint32_t width, const char *ascii,
                   const uint64_t *q_off, const uint32_t *q_ref, uint64_t n_q, uint64_t first, uint64_t total,
                   sa_result *out, cudaStream_t s, const sa_search_params *params, bool plain, uint32_t trunc_cap,
-                  Scratch &sc, int **flags_out) {
+                  Scratch &sc, int **flags_out, uint64_t *tile_kept = nullptr) {
     const uint32_t order = params ? params->flags & (SA_PARAM_KMER_ORDER | SA_PARAM_INPUT_ORDER) : 0u;
     if (order == (SA_PARAM_KMER_ORDER | SA_PARAM_INPUT_ORDER)) return SA_ERR_ARG;
     const uint32_t threads = params && params->threads_per_block ? params->threads_per_block : 1024;
@@ -320,6 +320,7 @@ int search_device(const sa_index *const *refs, uint32_t n_refs, uint32_t width, 
     L.rc_base = strand_bits ? (nwords + SA_TQ_PAD_WORDS) * 32 : 0;
     L.expire_waits = params && (params->flags & SA_PARAM_EXPIRE_WAITS);
     L.trunc_cap = trunc_cap;
+    L.tile_kept = tile_kept;
     L.ktotal = ktotal;
     L.qbucket = qbucket;
     L.bhist = bh;
@@ -355,7 +356,7 @@ int host_status(const int hflags[4]) {
 
 int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_bases, const uint64_t *q_offsets,
                 const uint32_t *q_ref, uint64_t n_q, sa_result *out, void *stream, const sa_search_params *params,
-                bool plain, uint32_t trunc_cap = ~0u) {
+                bool plain, uint32_t trunc_cap = ~0u, uint64_t *tile_kept = nullptr) {
     NvtxRange range(plain ? "sa_search_plain" : "sa_search");
     uint32_t width = 0;
     int st = check_refs(refs, n_refs, &width);
@@ -409,7 +410,7 @@ int search_impl(const sa_index *const *refs, uint32_t n_refs, const char *q_base
     if (err != cudaSuccess) return status_from_cuda(err);
     int *flags = nullptr;
     st = search_device(refs, n_refs, width, bases_d, off_d, ref_d, n_q, first, total, out_d, s, params, plain,
-                       trunc_cap, sc, &flags);
+                       trunc_cap, sc, &flags, tile_kept);
     if (st) return st;
     if (dstatus && (err = launch_search_status(flags, dstatus, s)) != cudaSuccess) return status_from_cuda(err);
     if (!out_dev) {
@@ -672,8 +673,10 @@ namespace sa {
 // 0) is added to every offset, for one chunk of a larger batch.
 int locate_device(const sa_index *const *refs, uint32_t n_refs, uint32_t width, const uint32_t *ref_d,
                   const sa_result *res_d, uint64_t n_q, uint32_t cap, uint64_t *off_d, void *pos_d,
-                  uint64_t capacity, const uint64_t *base_in, int *overflow, cudaStream_t s, Scratch &sc) {
-    uint64_t *partials = sc.get<uint64_t>(locate_tiles(n_q) + 1);
+                  uint64_t capacity, const uint64_t *base_in, int *overflow, cudaStream_t s, Scratch &sc,
+                  uint64_t *presummed = nullptr) {
+    // presummed: the tile sums, already added up by the search kernels
+    uint64_t *partials = presummed ? presummed : sc.get<uint64_t>(locate_tiles(n_q) + 1);
     if (sc.failed) return SA_ERR_NOMEM;
     LocateLaunch L;
     memset(&L, 0, sizeof L);
@@ -688,6 +691,7 @@ int locate_device(const sa_index *const *refs, uint32_t n_refs, uint32_t width, 
     L.out_pos = pos_d;
     L.capacity = pos_d ? capacity : 0;
     L.partials = partials;
+    L.presummed = presummed != nullptr;
     L.overflow = overflow;
     L.base_in = base_in;
     return status_from_cuda(launch_locate(L, s));
@@ -695,7 +699,7 @@ int locate_device(const sa_index *const *refs, uint32_t n_refs, uint32_t width, 
 
 int locate_impl(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_ref, const sa_result *res,
                 uint64_t n_q, uint32_t cap, uint64_t *out_offsets, void *out_pos, uint64_t out_pos_capacity,
-                void *stream, int *dstatus = nullptr) {
+                void *stream, int *dstatus = nullptr, uint64_t *presummed = nullptr) {
     NvtxRange range("sa_locate");
     uint32_t width = 0;
     int st = check_refs(refs, n_refs, &width);
@@ -717,7 +721,7 @@ int locate_impl(const sa_index *const *refs, uint32_t n_refs, const uint32_t *q_
     if (err != cudaSuccess) return status_from_cuda(err);
     if (overflow && (err = cudaMemsetAsync(overflow, 0, sizeof(int), s)) != cudaSuccess) return status_from_cuda(err);
     st = locate_device(refs, n_refs, width, ref_d, res_d, n_q, cap, off_d, pos_d, out_pos_capacity, nullptr, overflow,
-                       s, sc);
+                       s, sc, presummed);
     if (st) return st;
     if (overflow && (err = launch_capacity_status(overflow, dstatus, s)) != cudaSuccess) return status_from_cuda(err);
     if (!off_dev || !pos_dev) {
@@ -955,12 +959,21 @@ int sa_search_locate(const sa_index *const *refs, uint32_t n_refs, const char *q
         return search_pipelined_entry(refs, n_refs, q_bases, q_offsets, q_ref, n_q, out, stream, params, true, cap,
                                       out_offsets, out_pos, out_pos_capacity);
     NvtxRange range("sa_search_locate");
-    const int st = search_impl(refs, n_refs, q_bases, q_offsets, q_ref, n_q, out, stream, params, false, cap);
+    // the locate's tile sums, added up by the search kernels as they store
+    // each result (so the locate need not read every result for them)
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Scratch sc{s};
+    uint64_t *tile_kept = sc.get<uint64_t>(locate_tiles(n_q) + 1);
+    if (sc.failed) return SA_ERR_NOMEM;
+    cudaError_t err = cudaMemsetAsync(tile_kept, 0, (locate_tiles(n_q) + 1) * sizeof(uint64_t), s);
+    if (err != cudaSuccess) return status_from_cuda(err);
+    const int st = search_impl(refs, n_refs, q_bases, q_offsets, q_ref, n_q, out, stream, params, false, cap,
+                               tile_kept);
     if (st && st != SA_ERR_BASE && st != SA_ERR_ARG) return st;
     // invalid queries carry the all-ones result (no positions); the rest are located
     int *dstatus = params ? params->device_status : nullptr;
-    const int lst =
-        locate_impl(refs, n_refs, q_ref, out, n_q, cap, out_offsets, out_pos, out_pos_capacity, stream, dstatus);
+    const int lst = locate_impl(refs, n_refs, q_ref, out, n_q, cap, out_offsets, out_pos, out_pos_capacity, stream,
+                                dstatus, st == SA_OK ? tile_kept : nullptr);
     return lst ? lst : st;
 }
 

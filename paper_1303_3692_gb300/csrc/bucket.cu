@@ -106,11 +106,11 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_count_kernel(const __gr
         }
         uint16_t b = kNoQuery;
         if (!ok) {
-            store_result(a.out, q, ~0ull, ~0ull, a.trunc_cap);
+            store_result_sum(a, q, ~0ull, ~0ull);
         } else {
             const BucketRef d = sref[kSingle ? 0u : r];
             if (m == 0) {
-                store_result(a.out, q, 0, d.n, a.trunc_cap);
+                store_result_sum(a, q, 0, d.n);
             } else if (d.kmer_k != 0 && m >= d.kmer_k) {
                 const uint64_t x = w0 >> (64u - 2u * d.kmer_k);
                 b = (uint16_t)(((d.kbase + x) * kNumBuckets) / a.ktotal);

@@ -160,9 +160,9 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
         uint32_t R = look ? h.y : d.n;
 
         bool done = !live || !ok || m == 0 || (look && R - L <= 1u);
-        if (live && !ok) store_result(a.out, q, ~0ull, ~0ull, a.trunc_cap);
-        if (live && ok && m == 0) store_result(a.out, q, 0, d.n, a.trunc_cap);
-        if (live && ok && m > 0 && look && R - L <= 1u) store_result(a.out, q, R, R, a.trunc_cap);
+        if (live && !ok) store_result_sum(a, q, ~0ull, ~0ull);
+        if (live && ok && m == 0) store_result_sum(a, q, 0, d.n);
+        if (live && ok && m > 0 && look && R - L <= 1u) store_result_sum(a, q, R, R);
 
         uint32_t lcpL = 0, lcpR = 0, HL = 0, HR = 0, hlcpL = 0, hlcpR = 0, lo = 0, phase = 0;
         bool go = !done && look;
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
                     phase = 2;
                 }
                 if (R - L <= 1u) {
-                    store_result(a.out, q, phase == 0 ? R : lo, R, a.trunc_cap);
+                    store_result_sum(a, q, phase == 0 ? R : lo, R);
                     done = true;
                     go = false;
                 }

@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_gather_kernel(const __gr
 uint64_t locate_tiles(uint64_t n_q) { return (n_q + kTile - 1) / kTile; }
 
 static_assert(kTile == 4096, "the static scratch below is sized for 4096-query tiles");
+static_assert(kTile == (1ull << kLocateTileShift), "the search kernels sum kept counts per locate tile");
 
 cudaError_t locate_static_partials(uint64_t **ptr, uint64_t *entries) {
     static std::mutex mu;
@@ -210,7 +211,7 @@ cudaError_t launch_locate(const LocateLaunch &L, cudaStream_t s) {
     if (tiles == 0) {
         return cudaMemsetAsync(L.out_offsets, 0, sizeof(uint64_t), s);
     }
-    tile_sums_kernel<<<(unsigned)tiles, kTileThreads, 0, s>>>(L.res, L.n_q, L.cap, L.partials);
+    if (!L.presummed) tile_sums_kernel<<<(unsigned)tiles, kTileThreads, 0, s>>>(L.res, L.n_q, L.cap, L.partials);
     scan_partials_kernel<<<1, 1024, 0, s>>>(L.partials, tiles, L.base_in);
     if (L.width == 4)
         tile_gather_kernel<uint32_t><<<(unsigned)tiles, kTileThreads, 0, s>>>(L);

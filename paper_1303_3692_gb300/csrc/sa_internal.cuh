@@ -446,7 +446,25 @@ struct SearchLaunch {
     uint16_t *qbucket;        // per query: its bucket
     uint32_t *bhist;          // kNumBuckets + 1 bucket totals (zeroed by the caller)
     uint32_t *bcursor;        // kNumBuckets + 1 next free worklist slots
+    // search + locate in one call: per 2^kLocateTileShift queries, the sum of
+    // min(count, trunc_cap) of their results (zeroed by the caller), or null
+    uint64_t *tile_kept;
 };
+
+// Queries per tile of the locate's scan (locate.cu).
+constexpr uint32_t kLocateTileShift = 12;
+
+// store_result for the search kernels; in a search + locate call it also
+// adds the query's kept count min(count, cap) to its locate tile's sum, so
+// the locate need not read every result to find the tile sums.
+__device__ __forceinline__ void store_result_sum(const SearchLaunch &a, uint64_t q, uint64_t lo, uint64_t hi) {
+    store_result(a.out, q, lo, hi, a.trunc_cap);
+    if (a.tile_kept != nullptr && lo != ~0ull) {
+        const uint64_t k = hi - lo < (uint64_t)a.trunc_cap ? hi - lo : (uint64_t)a.trunc_cap;
+        if (k) atomicAdd(reinterpret_cast<unsigned long long *>(a.tile_kept) + (q >> kLocateTileShift),
+                         (unsigned long long)k);
+    }
+}
 // Worklist record of a query the first pass did not finish (64 bytes):
 //   {L, R, m, q}            a bracket (L, R) holding both bounds (L = -1 is
 //                           0xFFFFFFFF), the length and the query's index
@@ -486,6 +504,7 @@ struct LocateLaunch {
     void *out_pos;
     uint64_t capacity;
     uint64_t *partials;       // scratch: one entry per scan tile + 1
+    bool presummed;           // partials already hold the tile sums (from the search kernels)
     int *overflow;            // optional device flag: a position fell at or beyond capacity
     const uint64_t *base_in;  // optional device value added to every offset (a chunk of a larger batch)
 };

@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(1024, 1) search_kernel(const __grid_constant__
             }
             if (R - L <= 1u) {
                 const uint32_t lo_out = phase == 0 ? R : lo;
-                store_result(a.out, qout, lo_out, R, a.trunc_cap);
+                store_result_sum(a, qout, lo_out, R);
                 active = false;
             }
         }
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(256) search_plain_kernel(const __grid_constant
     if (bad || r >= a.n_refs) {
         if (bad) atomicOr(a.pack_err, 1);
         if (!bad) atomicOr(a.bad_ref, 1);
-        store_result(a.out, q, ~0ull, ~0ull, a.trunc_cap);
+        store_result_sum(a, q, ~0ull, ~0ull);
         return;
     }
     const uint32_t m = (uint32_t)(a1 - a0);
@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(256) search_plain_kernel(const __grid_constant
         else
             hi = mid;
     }
-    store_result(a.out, q, first, lo, a.trunc_cap);
+    store_result_sum(a, q, first, lo);
 }
 
 __global__ void search_status_kernel(const int *flags, int *dst) {
