@@ -42,16 +42,16 @@ WORKLOAD = "repetitive-100Mbp-10M-q100-locate64"
 # oracle_probe_model_kmer on 20,000 seeded queries: 1.19375 record probes per
 # query, 0.41265 of them after the one that comes with the 64-byte k-mer entry,
 # 6.58 occurrences on average, 0.51 positions kept at cap 64):
-#   pack_batch_kernel: 100 ASCII bytes read + 25 packed bytes and 12.5 bytes of
-#       per-base validity masks written                         = 137.5
+#   pack_batch_kernel: 100 ASCII bytes read + 25 packed bytes written (a batch
+#       without a non-base byte needs no validity masks)        = 125
 #   search (front_kernel + search_kernel): 8 offset bytes + 25 packed query
-#       bytes + 12.5 validity bytes + one 64-byte k-mer entry + 32 per further
-#       record probe + one 32-byte result                      = 154.7
+#       bytes + one 64-byte k-mer entry + 32 per further record probe + one
+#       32-byte result                                          = 142.2
 #   locate (3 kernels): 32 result bytes read + 8 offset bytes written + 4.1
 #       position bytes (suffix-array entry read and written)   = 44.1
 KERNEL_BYTES_PER_QUERY = {
-    "pack_batch_kernel": 100 + 25 + 12.5,
-    "search": 8 + 25 + 12.5 + 64 + 32 * 0.41265 + 32,
+    "pack_batch_kernel": 100 + 25,  # a clean batch: no validity masks written
+    "search": 8 + 25 + 64 + 32 * 0.41265 + 32,
     "locate": 32 + 8 + 4.1072,
 }
 # Random DRAM accesses per query of the search phase (the k-mer entry, further
@@ -557,17 +557,19 @@ def human_byte_model(T, sa_h, w, k: int, cap: int, sample: int = 20000, seed: in
     m = per["m"]
     probes = 64 * per["entry"] + 32 * per["further"] + 32 * per["windows"] + 32  # + the 32-byte result
     if kmer_order:
-        # bucketing pass (offsets, packed bases and validity read, a 2-byte
-        # bucket id written), scatter pass (bucket id, offsets and packed
-        # bases read, a 64-byte record written), first pass reads the record
-        reorder = (8 + m / 4 + m / 8 + 2) + (2 + 8 + m / 4 + 64)
+        # bucketing pass (offsets and the first two packed words read -- a
+        # batch the packing found clean needs no validity masks -- and a
+        # 2-byte bucket id written), scatter pass (bucket id, offsets and
+        # packed bases read, a 64-byte record written), first pass reads the record
+        reorder = (8 + 16 + 2) + (2 + 8 + m / 4 + 64)
         search = reorder + 64 + probes
     else:
         reorder = 0.0
-        search = 8 + m / 4 + m / 8 + probes
+        search = 8 + m / 4 + probes
     return {
         "sample": int(c), "k": k,
-        "bytes_per_query": {"pack_batch_kernel": m + m / 4 + m / 8, "search": search,
+        # pack: ASCII read, packed words written (no validity masks for a clean batch)
+        "bytes_per_query": {"pack_batch_kernel": m + m / 4, "search": search,
                             "locate": 32 + 8 + 16 * per["kept"]},
         # random sectors per query: 2 for the 64-byte entry, 1 per record, 1 per text window
         "random_sectors_per_query": 2 * per["entry"] + per["further"] + per["windows"],

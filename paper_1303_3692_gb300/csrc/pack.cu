@@ -54,7 +54,9 @@ cudaError_t launch_pack_text(const char *ascii, uint64_t n, uint64_t *words, uin
 // starts on a 16-byte boundary a full word is two 16-byte loads, so the reads
 // are fully coalesced.  Words past the batch (padding) are zero.
 __global__ void pack_batch_kernel(const uint8_t *__restrict__ ascii, uint64_t total, uint64_t nwords,
-                                  uint64_t *__restrict__ tq, uint32_t *__restrict__ tv, bool aligned16, int *dirty) {
+                                  uint64_t *__restrict__ tq, uint32_t *__restrict__ tv, bool aligned16, int *dirty,
+                                  const int *only_if_dirty) {
+    if (only_if_dirty != nullptr && *only_if_dirty == 0) return;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords + SA_TQ_PAD_WORDS; w += stride) {
         if (w >= nwords) {
@@ -82,7 +84,7 @@ __global__ void pack_batch_kernel(const uint8_t *__restrict__ ascii, uint64_t to
             for (uint32_t j = 0; j < 32 && b0 + j < total; j++)
                 if (base_code(ascii[b0 + j]) > 3) mask |= 1u << j;
         }
-        tv[w] = mask;
+        if (dirty == nullptr || mask != 0u) tv[w] = mask;
         if (mask != 0u && dirty != nullptr) atomicOr(dirty, 1);
     }
 }
@@ -94,7 +96,9 @@ __global__ void pack_batch_kernel(const uint8_t *__restrict__ ascii, uint64_t to
 // are complemented (c -> 3 - c, i.e. every bit flipped) and put in reverse
 // order; its validity mask is reversed the same way.
 __global__ void pack_batch_rc_kernel(const uint8_t *__restrict__ ascii, uint64_t total, uint64_t nwords,
-                                     uint64_t *__restrict__ tq, uint32_t *__restrict__ tv, int *dirty) {
+                                     uint64_t *__restrict__ tq, uint32_t *__restrict__ tv, int *dirty,
+                                     const int *only_if_dirty) {
+    if (only_if_dirty != nullptr && *only_if_dirty == 0) return;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords + SA_TQ_PAD_WORDS; w += stride) {
         if (w >= nwords) {
@@ -131,7 +135,7 @@ __global__ void pack_batch_rc_kernel(const uint8_t *__restrict__ ascii, uint64_t
             }
         }
         tq[w] = word;
-        tv[w] = mask;
+        if (dirty == nullptr || mask != 0u) tv[w] = mask;
         if (mask != 0u && dirty != nullptr) atomicOr(dirty, 1);
     }
 }
@@ -147,11 +151,26 @@ cudaError_t launch_pack_batch(const SearchLaunch &L, uint64_t *tq, uint32_t *tv,
     // first, the other from word nwords + SA_TQ_PAD_WORDS on) when each query
     // names its strand
     if (!L.revcomp || L.strand_bits)
-        pack_batch_kernel<<<blocks, threads, 0, s>>>(ascii, L.total, L.nwords, tq, tv, aligned, L.batch_dirty);
+        pack_batch_kernel<<<blocks, threads, 0, s>>>(ascii, L.total, L.nwords, tq, tv, aligned, L.batch_dirty,
+                                                     nullptr);
     if (L.revcomp || L.strand_bits) {
         const uint64_t half = L.strand_bits ? L.nwords + SA_TQ_PAD_WORDS : 0;
         pack_batch_rc_kernel<<<blocks, threads, 0, s>>>(ascii, L.total, L.nwords, tq + half, tv + half,
-                                                        L.batch_dirty);
+                                                        L.batch_dirty, nullptr);
+    }
+    // With a batch flag the passes above store only the masks of words that
+    // hold a non-base byte (the search reads no masks of a clean batch); a
+    // batch that is not clean is packed again with every mask (these
+    // launches return at once for a clean one).
+    if (L.batch_dirty != nullptr) {
+        if (!L.revcomp || L.strand_bits)
+            pack_batch_kernel<<<blocks, threads, 0, s>>>(ascii, L.total, L.nwords, tq, tv, aligned, nullptr,
+                                                         L.batch_dirty);
+        if (L.revcomp || L.strand_bits) {
+            const uint64_t half = L.strand_bits ? L.nwords + SA_TQ_PAD_WORDS : 0;
+            pack_batch_rc_kernel<<<blocks, threads, 0, s>>>(ascii, L.total, L.nwords, tq + half, tv + half, nullptr,
+                                                            L.batch_dirty);
+        }
     }
     return cudaGetLastError();
 }

@@ -429,7 +429,8 @@ struct SearchLaunch {
     sa_result *out;
     int *pack_err;            // device flag: some query had a non-ACGT byte or bad offsets
     int *batch_dirty;         // device flag set by the packing: some byte of the batch is not a base
-                              // (null: assume so); a clean batch needs no per-query validity check
+                              // (null: assume so).  With the flag, tv holds every mask only for a batch
+                              // that is not clean; a clean batch needs (and has) none.
     int *bad_ref;             // device flag: some query named a reference id >= n_refs
     unsigned long long *counter;
     int *status;

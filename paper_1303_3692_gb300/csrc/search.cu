@@ -383,7 +383,9 @@ __global__ void __launch_bounds__(256) search_plain_kernel(const __grid_constant
         a1 = a0 + len;
     }
     bool bad = !range_ok;
-    if (range_ok) {  // every base of the query must be one of A, C, G, T
+    // every base of the query must be one of A, C, G, T (nothing to check in
+    // a batch the packing found clean)
+    if (range_ok && (a.batch_dirty == nullptr || *a.batch_dirty != 0)) {
         for (uint64_t b = a0; b < a1; b++)
             if ((__ldg(a.tv + (b >> 5)) >> (b & 31u)) & 1u) bad = true;
     }
