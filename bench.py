@@ -875,7 +875,7 @@ def serve_on_index(idxs, q_bases, q_offsets, seconds: float, rate: float = 2000.
 # scatter, first pass, persistent pass) from one single-pass ncu capture of the
 # default bench command (the median of its 13 full-size steps), valid only
 # while the phase's sources hash to kernel_sha.
-HUMAN_TRAFFIC = {"kernel_sha": "65d6fd481eea41fb", "kernel": "search", "dram_bytes_per_launch": 78_734_595_072}
+HUMAN_TRAFFIC = {"kernel_sha": "3190073a61eb4234", "kernel": "search", "dram_bytes_per_launch": 76_690_287_872}
 
 
 def cpu_baseline_sa(T, sa_h, w, args, sa_note: str):
