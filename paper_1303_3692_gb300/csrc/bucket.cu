@@ -15,8 +15,10 @@
 // Three kernels put the batch in that order before the first pass (front.cu),
 // which then reads its queries from the list they write:
 //   bucket_count_kernel    one thread per query: offsets, strand, reference,
-//                          validity of every base (invalid and empty queries
-//                          get their results here), and the query's bucket --
+//                          validity of every base when the packing found a
+//                          non-base byte in the batch (invalid and empty
+//                          queries get their results here), and the query's
+//                          bucket --
 //                          its first k bases as a fraction of all k-mer
 //                          entries of the call's indexes, in kNumBuckets
 //                          equal slices, or the extra bucket of queries with

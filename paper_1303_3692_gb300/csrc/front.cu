@@ -3,9 +3,11 @@
 // Most queries of a batch are decided by their k-mer bracket and one or two
 // probes, so the first pass runs them straight through, one query per thread
 // and no shared state:
-//   * the query's first 128 bases come from the packed batch (five words of a
-//     38-byte-per-100-bases array that the packing kernel has just written,
-//     so they are L2 hits) and its validity from the batch's per-base masks;
+//   * in input order the query's first 128 bases come from the packed batch
+//     (five words of a 38-byte-per-100-bases array that the packing kernel
+//     has just written) and, when the packing found a non-base byte in the
+//     batch, its validity from the per-base masks; in k-mer order its record
+//     in the list (bucket.cu) holds its first 192 bases, already checked;
 //   * for m >= k one aligned 64-byte read of the k-mer entry of its first k
 //     bases x gives the bracket (lo - 1, hi) of the suffixes that sort
 //     between x and x + 1 and the suffix at the bracket's first pivot (its

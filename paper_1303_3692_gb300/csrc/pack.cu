@@ -50,7 +50,10 @@ cudaError_t launch_pack_text(const char *ascii, uint64_t n, uint64_t *words, uin
 // Packs a whole query batch as one text (the layout of the reference) and
 // records, per 32-base word, which bytes are not bases, so that the search
 // reads any window of any query with one text_window and checks a query's
-// validity from its own bytes only.  One thread per word; when the batch
+// validity from its own bytes only.  With a batch flag (dirty) a word's mask
+// is stored only when it holds a non-base byte, and the flag is raised; the
+// search then reads masks only for a batch whose flag is set, which the
+// launcher packs again with every mask (only_if_dirty).  One thread per word; when the batch
 // starts on a 16-byte boundary a full word is two 16-byte loads, so the reads
 // are fully coalesced.  Words past the batch (padding) are zero.
 __global__ void pack_batch_kernel(const uint8_t *__restrict__ ascii, uint64_t total, uint64_t nwords,
