@@ -159,7 +159,10 @@ typedef struct sa_search_params {
  * k-mer entry settles finishing in a one-thread-per-query first pass.  These
  * flags force one order (setting both is SA_ERR_ARG).  The default takes
  * k-mer order only for batches of at least 2^20 queries: a smaller batch is
- * in flight all at once whatever its order. */
+ * in flight all at once whatever its order.  A batch of 2^30 queries or more
+ * is always searched in input order.  K-mer order takes about 140 bytes of
+ * scratch per query for the ordered list (room for every bucket's estimated
+ * share and for queries the estimate missed). */
 #define SA_PARAM_KMER_ORDER 0x8u
 #define SA_PARAM_INPUT_ORDER 0x10u
 /* sa_search_params.flags: each query names its strand -- bit 31 of q_ref[q]

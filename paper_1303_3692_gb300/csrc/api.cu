@@ -177,7 +177,8 @@ bool use_kmer_order(const sa_index *const *refs, uint32_t n_refs, uint64_t n_q, 
         if (refs[r]->krt) ktotal += 1ull << (2 * refs[r]->kmer_k);
         index_bytes += refs[r]->device_bytes;
     }
-    if (ktotal == 0 || order == SA_PARAM_INPUT_ORDER) return false;
+    // (list slots are 32-bit: batches below 2^30 queries)
+    if (ktotal == 0 || order == SA_PARAM_INPUT_ORDER || n_q >= (1ull << 30)) return false;
     return order == SA_PARAM_KMER_ORDER || (index_bytes > kKmerOrderMinBytes && n_q >= kKmerOrderMinQueries);
 }
 
@@ -267,9 +268,8 @@ int search_device(const sa_index *const *refs, uint32_t n_refs, uint32_t width, 
     for (uint32_t r = 0; r < n_refs; r++)
         if (refs[r]->krt) ktotal += 1ull << (2 * refs[r]->kmer_k);
     const bool kmer_order = !plain && use_kmer_order(refs, n_refs, n_q, order);
-    uint16_t *qbucket = kmer_order ? sc.get<uint16_t>(n_q) : nullptr;
-    uint4 *wrec_in = kmer_order ? sc.get<uint4>(4 * n_q) : nullptr;
-    uint32_t *bh = kmer_order ? sc.get<uint32_t>(2 * (kNumBuckets + 1)) : nullptr;
+    uint4 *wrec_in = kmer_order ? sc.get<uint4>(4 * list_capacity(n_q)) : nullptr;
+    uint32_t *bplan = kmer_order ? sc.get<uint32_t>(kPlanWords) : nullptr;
     // [0] pack error, [1] status, [2] worklist count, [3] bad reference id,
     // [4] records of the k-mer-ordered list, [5] a non-base byte in the batch
     int *flags = sc.get<int>(8);
@@ -279,7 +279,7 @@ int search_device(const sa_index *const *refs, uint32_t n_refs, uint32_t width, 
     if ((err = cudaMemsetAsync(flags, 0, 8 * sizeof(int), s)) != cudaSuccess) return status_from_cuda(err);
     if ((err = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s)) != cudaSuccess)
         return status_from_cuda(err);
-    if (bh && (err = cudaMemsetAsync(bh, 0, (kNumBuckets + 1) * sizeof(uint32_t), s)) != cudaSuccess)
+    if (bplan && (err = cudaMemsetAsync(bplan, 0, kPlanWords * sizeof(uint32_t), s)) != cudaSuccess)
         return status_from_cuda(err);
     *flags_out = flags;
 
@@ -322,9 +322,7 @@ int search_device(const sa_index *const *refs, uint32_t n_refs, uint32_t width, 
     L.trunc_cap = trunc_cap;
     L.tile_kept = tile_kept;
     L.ktotal = ktotal;
-    L.qbucket = qbucket;
-    L.bhist = bh;
-    L.bcursor = bh ? bh + kNumBuckets + 1 : nullptr;
+    L.bplan = bplan;
     L.wrec_in = wrec_in;
     L.wl_in_count = reinterpret_cast<uint32_t *>(flags + 4);
     L.bad_ref = flags + 3;

@@ -55,6 +55,26 @@ __device__ __forceinline__ int cmp_entry(const uint64_t w[4], uint32_t m, const 
     return cmp_suffix_qw(T, n, pos, qw, m, 192u, lcp);
 }
 
+// The list slot of the j-th record of the k-mer-ordered list: region by
+// region (in the largest bucket b whose regions before it hold at most j
+// records), then the overflow region.  prefix: the exclusive sums of the
+// regions' fills (kNumBuckets + 2 entries, the last their total); start: each
+// region's first slot.
+__device__ __forceinline__ uint32_t list_slot(const uint32_t *prefix, const uint32_t *start, uint32_t ov_start,
+                                              uint32_t j) {
+    const uint32_t in_regions = prefix[kNumBuckets + 1];
+    if (j >= in_regions) return ov_start + (j - in_regions);
+    uint32_t lo = 0, hi = kNumBuckets + 1;  // prefix[lo] <= j < prefix[hi]
+    while (hi - lo > 1u) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (prefix[mid] <= j)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return start[lo] + (j - prefix[lo]);
+}
+
 // kFromList: the queries come from the k-mer-ordered list of bucket.cu (one
 // 64-byte record each: length, index, reference, first base in the packed
 // batch and first 192 bases, already checked) instead of the batch's offsets.
@@ -62,10 +82,17 @@ template <bool kSingle, bool kFromList>
 __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_constant__ SearchLaunch a) {
     __shared__ FrontDesc sdesc[SA_MAX_REFS];
     __shared__ uint4 s_stage[kFrontThreads / 32][32][4];  // worklist records staged per warp
+    __shared__ uint32_t s_lprefix[kNumBuckets + 2];        // the list's numbering (list input)
+    __shared__ uint32_t s_lstart[kNumBuckets + 1];
     for (unsigned r = threadIdx.x; r < a.n_refs; r += blockDim.x) {
         const RefDesc &d = a.refs.r[r];
         sdesc[r] = FrontDesc{d.text, d.rec, d.krt, (uint32_t)d.n, d.kmer_k};
     }
+    if (kFromList) {
+        for (unsigned i = threadIdx.x; i < kNumBuckets + 2; i += blockDim.x) s_lprefix[i] = a.bplan[kPlanPrefix + i];
+        for (unsigned i = threadIdx.x; i <= kNumBuckets; i += blockDim.x) s_lstart[i] = a.bplan[kPlanStart + i];
+    }
+    const uint32_t ov_start = kFromList ? a.bplan[kPlanOvStart] : 0u;
     __syncthreads();
 
     const unsigned lane = threadIdx.x & 31u;
@@ -108,9 +135,11 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
         uint32_t r, m;
         bool ok, entry = true;
         uint64_t w[4];
+        uint32_t lslot = 0;  // the record's slot in the list (list input)
         if (kFromList) {
             uint4 c0, c1, c2, c3;
-            const uint4 *src = a.wrec_in + 4 * (size_t)(base + lane);
+            if (live) lslot = list_slot(s_lprefix, s_lstart, ov_start, (uint32_t)(base + lane));
+            const uint4 *src = a.wrec_in + 4 * (size_t)lslot;
             ldg32_if(live, src, &c0, &c1);
             ldg32_if(live, src + 2, &c2, &c3);
             m = c0.x;
@@ -171,7 +200,7 @@ __global__ void __launch_bounds__(kFrontThreads, 4) front_kernel(const __grid_co
         // in list order, bases 128-191 are the record's last 16 bytes (read
         // again when a compare gets there: an L1 or L2 hit)
         const QueryWindows qw{tq, qa, w[3],
-                              kFromList ? reinterpret_cast<const uint64_t *>(a.wrec_in + 4 * (size_t)(base + lane) + 3)
+                              kFromList ? reinterpret_cast<const uint64_t *>(a.wrec_in + 4 * (size_t)lslot + 3)
                                         : nullptr,
                               kFromList ? 2u : 0u};
         // One compare's outcome c at pivot M with common prefix l.

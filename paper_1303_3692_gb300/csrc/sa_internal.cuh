@@ -54,6 +54,25 @@ constexpr uint32_t kNumBuckets = 256;
 //       words past the query's end are not its bases)
 constexpr uint32_t kListNeedsEntry = 0x80000000u;
 constexpr uint64_t kListMaxBase = 1ull << 48;
+// The list's plan (bucket.cu), 32-bit words: every kListSampleStride-th
+// query's bucket counted; from those counts each bucket's region of the list
+// (start, capacity) and a cursor; after the scatter, the exclusive prefix
+// sums of the regions' fills (kNumBuckets + 2 words, the last the sum); and
+// the overflow region that takes what does not fit a bucket's region.
+constexpr uint32_t kListSampleStride = 32;
+constexpr uint32_t kPlanSample = 0;
+constexpr uint32_t kPlanStart = kPlanSample + kNumBuckets + 1;
+constexpr uint32_t kPlanCap = kPlanStart + kNumBuckets + 1;
+constexpr uint32_t kPlanCursor = kPlanCap + kNumBuckets + 1;
+constexpr uint32_t kPlanPrefix = kPlanCursor + kNumBuckets + 1;
+constexpr uint32_t kPlanOvStart = kPlanPrefix + kNumBuckets + 2;
+constexpr uint32_t kPlanOvCursor = kPlanOvStart + 1;
+constexpr uint32_t kPlanWords = kPlanOvCursor + 1;
+// Records the list needs room for, at most: every bucket's region (the sample
+// counts scaled up by 9/8, plus 256) and an overflow region for every query.
+__host__ __device__ constexpr uint64_t list_capacity(uint64_t n_q) {
+    return (n_q + kListSampleStride) * 9 / 8 + 256ull * (kNumBuckets + 1) + n_q;
+}
 
 // The compare outcome of the three cases of Section IV.
 enum : int { CMP_LESS = -1, CMP_PREFIX = 0, CMP_GREATER = 1 };
@@ -444,9 +463,7 @@ struct SearchLaunch {
     uint32_t trunc_cap;       // the locate cap of sa_search_locate (SA_RESULT_TRUNCATED), else ~0u
     // k-mer order (bucket.cu)
     uint64_t ktotal;          // k-mer entries of all indexes of the call
-    uint16_t *qbucket;        // per query: its bucket
-    uint32_t *bhist;          // kNumBuckets + 1 bucket totals (zeroed by the caller)
-    uint32_t *bcursor;        // kNumBuckets + 1 next free worklist slots
+    uint32_t *bplan;          // the list's plan, kPlanWords words (see below; zeroed by the caller)
     // search + locate in one call: per 2^kLocateTileShift queries, the sum of
     // min(count, trunc_cap) of their results (zeroed by the caller), or null
     uint64_t *tile_kept;

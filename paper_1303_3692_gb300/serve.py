@@ -55,10 +55,12 @@ def scratch_bytes(n_q: int, n_bases: int, both_strands: bool = False) -> int:
     """Device scratch one search call takes from the library's pool, at most:
     the packed batch (8 bytes per 32 bases) and its validity masks (4 bytes
     per 32 bases), twice when queries name their strands; 64 bytes of worklist
-    room per query; in k-mer order another 64-byte record and a 2-byte bucket
-    per query; small flags, and 256 bytes of alignment per allocation."""
+    room per query; in k-mer order the ordered list (64-byte records, room
+    for about 2.125 per query plus 257 * 256); small flags, and 256 bytes of
+    alignment per allocation."""
     words = ((n_bases + 31) // 32 + 6) * (2 if both_strands else 1)
-    return 12 * words + 64 * n_q + 66 * n_q + 2 * 257 * 4 + 80 + 8 * 256
+    listed = ((n_q + 32) * 9 // 8 + 256 * 257 + n_q) * 64
+    return 12 * words + 64 * n_q + listed + 1288 * 4 + 80 + 8 * 256
 
 
 def kept(counts: np.ndarray, cap: int) -> np.ndarray:

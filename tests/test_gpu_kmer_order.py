@@ -185,3 +185,42 @@ def test_strand_per_query(sa, order):
     for q in range(0, n_q, 13):
         want = oracle.locate(sas[q_ref[q]], int(got[q, 0]), int(got[q, 1]), 4)
         assert np.array_equal(pos[offs[q]:offs[q + 1]].astype(np.int64), want)
+
+
+def test_kmer_order_overflow_region(sa):
+    """The list's bucket regions are sized from every 32nd query.  Here those
+    queries all start with A and every other query with T, so the T buckets
+    get the minimum room and most of their records go to the overflow region:
+    the results stay bit-exact, with locate too."""
+    ref = datagen.reference(300_000, 95, gc=0.5, sd_cover=0.05)
+    qb, qo, _ = datagen.queries(ref, 120_000, 96, m=(20, 160), frac_sampled=0.9, subs=(0, 1))
+    qs = [bytes(qb[qo[i]:qo[i + 1]]) for i in range(qo.size - 1)]
+    a_q = [x for x in qs if x[:1] == b"A"]
+    t_q = [x for x in qs if x[:1] == b"T"]
+    n = 32 * min(len(a_q), len(t_q) // 31)
+    order = []
+    ai = ti = 0
+    for i in range(n):
+        if i % 32 == 0:
+            order.append(a_q[ai])
+            ai += 1
+        else:
+            order.append(t_q[ti])
+            ti += 1
+    qb2 = np.frombuffer(b"".join(order), dtype=np.uint8).copy()
+    qo2 = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum([len(x) for x in order], out=qo2[1:])
+    idx = sa.sa_build(torch.from_numpy(ref).cuda())
+    got = _both(sa, idx, qb2, qo2)
+    T = oracle.normalize(ref)
+    lo, hi = oracle.search_batch(T, oracle.sa_naive(T), qb2, qo2, threads=oracle.cpu_threads())
+    assert np.array_equal(got[:, 0], lo) and np.array_equal(got[:, 1], hi)
+    # the fused search + locate through the overflow region as well
+    for flags in (sa.SA_PARAM_KMER_ORDER, sa.SA_PARAM_INPUT_ORDER):
+        p = sa.sa_search_params(flags=flags)
+        r, o, pos = sa.sa_search_locate(idx, torch.from_numpy(qb2).cuda(), torch.from_numpy(qo2).cuda(), 4, params=p)
+        if flags == sa.SA_PARAM_KMER_ORDER:
+            want = (r.cpu().numpy(), o.cpu().numpy(), pos.cpu().numpy())
+        else:
+            assert np.array_equal(r.cpu().numpy(), want[0]) and np.array_equal(o.cpu().numpy(), want[1])
+            assert np.array_equal(pos.cpu().numpy()[:int(want[1][-1])], want[2][:int(want[1][-1])])
