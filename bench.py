@@ -557,11 +557,11 @@ def human_byte_model(T, sa_h, w, k: int, cap: int, sample: int = 20000, seed: in
     m = per["m"]
     probes = 64 * per["entry"] + 32 * per["further"] + 32 * per["windows"] + 32  # + the 32-byte result
     if kmer_order:
-        # bucketing pass (offsets and the first two packed words read -- a
-        # batch the packing found clean needs no validity masks -- and a
-        # 2-byte bucket id written), scatter pass (bucket id, offsets and
-        # packed bases read, a 64-byte record written), first pass reads the record
-        reorder = (8 + 16 + 2) + (2 + 8 + m / 4 + 64)
+        # sampling pass (offsets and the first two packed words of every 32nd
+        # query), scatter pass (offsets and packed bases read -- a batch the
+        # packing found clean needs no validity masks -- and a 64-byte record
+        # written), first pass reads the record
+        reorder = (8 + 16) / 32 + (8 + m / 4 + 64)
         search = reorder + 64 + probes
     else:
         reorder = 0.0
@@ -871,11 +871,11 @@ def serve_on_index(idxs, q_bases, q_offsets, seconds: float, rate: float = 2000.
     return out
 
 
-# DRAM bytes (read + write) of one 3.1 Gbp search phase (bucket count, scan and
-# scatter, first pass, persistent pass) from one single-pass ncu capture of the
+# DRAM bytes (read + write) of one 3.1 Gbp search phase (bucket sample, plan,
+# scatter and fill, first pass, persistent pass) from one single-pass ncu capture of the
 # default bench command (the median of its 13 full-size steps), valid only
 # while the phase's sources hash to kernel_sha.
-HUMAN_TRAFFIC = {"kernel_sha": "3190073a61eb4234", "kernel": "search", "dram_bytes_per_launch": 76_690_287_872}
+HUMAN_TRAFFIC = {"kernel_sha": "6a67bbb9eec6b52f", "kernel": "search", "dram_bytes_per_launch": 72_608_646_400}
 
 
 def cpu_baseline_sa(T, sa_h, w, args, sa_note: str):

@@ -321,6 +321,7 @@ int search_device(const sa_index *const *refs, uint32_t n_refs, uint32_t width, 
     L.expire_waits = params && (params->flags & SA_PARAM_EXPIRE_WAITS);
     L.trunc_cap = trunc_cap;
     L.tile_kept = tile_kept;
+    L.tile_sum_by_warp = !kmer_order;
     L.ktotal = ktotal;
     L.bplan = bplan;
     L.wrec_in = wrec_in;

@@ -467,6 +467,7 @@ struct SearchLaunch {
     // search + locate in one call: per 2^kLocateTileShift queries, the sum of
     // min(count, trunc_cap) of their results (zeroed by the caller), or null
     uint64_t *tile_kept;
+    bool tile_sum_by_warp;    // input order: the lanes storing together mostly share a tile
 };
 
 // Queries per tile of the locate's scan (locate.cu).
@@ -475,12 +476,22 @@ constexpr uint32_t kLocateTileShift = 12;
 // store_result for the search kernels; in a search + locate call it also
 // adds the query's kept count min(count, cap) to its locate tile's sum, so
 // the locate need not read every result to find the tile sums.
+// In input order the lanes storing at the same time hold consecutive queries,
+// so those sharing a tile add their counts with one atomic; in k-mer order
+// each lane adds its own.
 __device__ __forceinline__ void store_result_sum(const SearchLaunch &a, uint64_t q, uint64_t lo, uint64_t hi) {
     store_result(a.out, q, lo, hi, a.trunc_cap);
-    if (a.tile_kept != nullptr && lo != ~0ull) {
-        const uint64_t k = hi - lo < (uint64_t)a.trunc_cap ? hi - lo : (uint64_t)a.trunc_cap;
-        if (k) atomicAdd(reinterpret_cast<unsigned long long *>(a.tile_kept) + (q >> kLocateTileShift),
-                         (unsigned long long)k);
+    if (a.tile_kept == nullptr) return;
+    const uint64_t c = lo == ~0ull ? 0ull : hi - lo;
+    const uint32_t k = c < (uint64_t)a.trunc_cap ? (uint32_t)c : a.trunc_cap;
+    const uint64_t tile = q >> kLocateTileShift;
+    unsigned long long *sum_at = reinterpret_cast<unsigned long long *>(a.tile_kept) + tile;
+    if (a.tile_sum_by_warp) {
+        const unsigned same = __match_any_sync(__activemask(), tile);
+        const uint32_t sum = __reduce_add_sync(same, k);
+        if (sum != 0u && (threadIdx.x & 31u) == (unsigned)(__ffs(same) - 1)) atomicAdd(sum_at, (unsigned long long)sum);
+    } else if (k != 0u) {
+        atomicAdd(sum_at, (unsigned long long)k);
     }
 }
 // Worklist record of a query the first pass did not finish (64 bytes):
