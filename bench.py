@@ -875,7 +875,7 @@ def serve_on_index(idxs, q_bases, q_offsets, seconds: float, rate: float = 2000.
 # scatter and fill, first pass, persistent pass) from one single-pass ncu capture of the
 # default bench command (the median of its 13 full-size steps), valid only
 # while the phase's sources hash to kernel_sha.
-HUMAN_TRAFFIC = {"kernel_sha": "6a67bbb9eec6b52f", "kernel": "search", "dram_bytes_per_launch": 72_608_646_400}
+HUMAN_TRAFFIC = {"kernel_sha": "fc28c78cf4b08d9b", "kernel": "search", "dram_bytes_per_launch": 72_274_846_976}
 
 
 def cpu_baseline_sa(T, sa_h, w, args, sa_note: str):
