@@ -101,3 +101,22 @@ def test_host_pipeline_reports_bad_bases(env):
     assert e.value.status == sa.SA_ERR_BASE
     assert out[q, 3] == sa.SA_RESULT_INVALID and (out[q, :3] == -1).all()
     assert out[q - 1, 3] != sa.SA_RESULT_INVALID
+
+
+def test_host_pipeline_kmer_order(env):
+    """The chunked host path in k-mer order (forced here; the library takes it
+    by itself only for indexes above 48 GB), with locate: every chunk's
+    k-mer-ordered list and located positions give the device path's results."""
+    sa, refs, idxs, qb, qo = env
+    cap = 8
+    p = sa.sa_search_params(flags=sa.SA_PARAM_KMER_ORDER)
+    want_r, want_o, want_p = _device(sa, idxs[0], qb, qo, cap)
+    total = int(want_o[-1])
+    res = torch.empty((N_Q, sa.RESULT_FIELDS), dtype=torch.int64).pin_memory()
+    offs = torch.empty(N_Q + 1, dtype=torch.int64).pin_memory()
+    pos = torch.empty(total, dtype=torch.int32).pin_memory()
+    sa.sa_search_locate(idxs[0], torch.from_numpy(qb).pin_memory(), torch.from_numpy(qo).pin_memory(), cap,
+                        out=res, out_offsets=offs, out_pos=pos, capacity=total, params=p)
+    assert np.array_equal(res.numpy(), want_r)
+    assert np.array_equal(offs.numpy(), want_o)
+    assert np.array_equal(pos.numpy(), want_p[:total])
